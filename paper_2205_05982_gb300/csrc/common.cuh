@@ -1,0 +1,355 @@
+// Shared device/host definitions of the vqsort CUDA library: key codes,
+// the order-preserving codec, memory-model and TMA helpers, and the
+// workspace layout that the host driver and the kernels agree on.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vq {
+
+// ---------------------------------------------------------------------------
+// Keys in registers ("codes"): every key type is mapped to an unsigned code
+// whose unsigned order is the requested sort order (Sec. 2.4 orders; IEEE
+// totalOrder for floats). Kernels only ever sort codes ascending.
+// ---------------------------------------------------------------------------
+
+struct U128 {
+  uint64_t lo, hi;
+};
+
+template <int KB> struct KT;
+template <> struct KT<2> {   // i16 / u16: 16-bit code held in a 32-bit register
+  using Code = uint32_t;
+  using Mem = uint16_t;
+  static __host__ __device__ Code max_code() { return 0xFFFFu; }
+};
+template <> struct KT<4> {
+  using Code = uint32_t;
+  using Mem = uint32_t;
+  static __host__ __device__ Code max_code() { return 0xFFFFFFFFu; }
+};
+template <> struct KT<8> {
+  using Code = uint64_t;
+  using Mem = uint64_t;
+  static __host__ __device__ Code max_code() { return ~0ull; }
+};
+template <> struct KT<16> {   // u128 and kv64: {lo, hi} words
+  using Code = U128;
+  using Mem = U128;
+  static __host__ __device__ Code max_code() { return U128{~0ull, ~0ull}; }
+};
+
+__host__ __device__ __forceinline__ bool lt(uint32_t a, uint32_t b) { return a < b; }
+__host__ __device__ __forceinline__ bool lt(uint64_t a, uint64_t b) { return a < b; }
+// Algorithm 2: the upper word decides unless equal, then the lower word.
+__host__ __device__ __forceinline__ bool lt(const U128 &a, const U128 &b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__host__ __device__ __forceinline__ bool eq(uint32_t a, uint32_t b) { return a == b; }
+__host__ __device__ __forceinline__ bool eq(uint64_t a, uint64_t b) { return a == b; }
+__host__ __device__ __forceinline__ bool eq(const U128 &a, const U128 &b) {
+  return a.hi == b.hi && a.lo == b.lo;
+}
+
+template <class C> __device__ __forceinline__ C cmin(const C &a, const C &b) { return lt(b, a) ? b : a; }
+template <class C> __device__ __forceinline__ C cmax(const C &a, const C &b) { return lt(b, a) ? a : b; }
+
+// Compare-and-exchange: a <- min, b <- max.
+template <class C> __device__ __forceinline__ void cas(C &a, C &b) {
+  C lo = cmin(a, b), hi = cmax(a, b);
+  a = lo;
+  b = hi;
+}
+
+__device__ __forceinline__ uint32_t shfl_xor(uint32_t v, int m) { return __shfl_xor_sync(0xFFFFFFFFu, v, m); }
+__device__ __forceinline__ uint64_t shfl_xor(uint64_t v, int m) { return __shfl_xor_sync(0xFFFFFFFFu, v, m); }
+__device__ __forceinline__ U128 shfl_xor(const U128 &v, int m) {
+  return U128{__shfl_xor_sync(0xFFFFFFFFu, v.lo, m), __shfl_xor_sync(0xFFFFFFFFu, v.hi, m)};
+}
+__device__ __forceinline__ uint32_t shfl_idx(uint32_t v, int l) { return __shfl_sync(0xFFFFFFFFu, v, l); }
+__device__ __forceinline__ uint64_t shfl_idx(uint64_t v, int l) { return __shfl_sync(0xFFFFFFFFu, v, l); }
+__device__ __forceinline__ U128 shfl_idx(const U128 &v, int l) {
+  return U128{__shfl_sync(0xFFFFFFFFu, v.lo, l), __shfl_sync(0xFFFFFFFFu, v.hi, l)};
+}
+
+// Code one below c (c > 0): used to split "< p" from "== p" after a
+// degenerate partition.
+__host__ __device__ __forceinline__ uint32_t pred(uint32_t c) { return c - 1; }
+__host__ __device__ __forceinline__ uint64_t pred(uint64_t c) { return c - 1; }
+__host__ __device__ __forceinline__ U128 pred(const U128 &c) {
+  return U128{c.lo - 1, c.lo == 0 ? c.hi - 1 : c.hi};
+}
+
+// ---------------------------------------------------------------------------
+// Codec: raw key bits <-> code. kind: 0 unsigned, 1 signed integer,
+// 2 IEEE float, 3 kv64 (word swap so the key is the upper half).
+// desc complements the code so descending becomes ascending.
+// ---------------------------------------------------------------------------
+struct Codec {
+  int kind;
+  int desc;
+};
+
+template <int KB> __host__ __device__ __forceinline__ typename KT<KB>::Code encode(typename KT<KB>::Code x, Codec cd);
+template <int KB> __host__ __device__ __forceinline__ typename KT<KB>::Code decode(typename KT<KB>::Code x, Codec cd);
+
+template <> __host__ __device__ __forceinline__ uint32_t encode<2>(uint32_t x, Codec cd) {
+  if (cd.kind == 1) x ^= 0x8000u;
+  if (cd.desc) x ^= 0xFFFFu;
+  return x;
+}
+template <> __host__ __device__ __forceinline__ uint32_t decode<2>(uint32_t x, Codec cd) {
+  if (cd.desc) x ^= 0xFFFFu;
+  if (cd.kind == 1) x ^= 0x8000u;
+  return x;
+}
+template <> __host__ __device__ __forceinline__ uint32_t encode<4>(uint32_t x, Codec cd) {
+  if (cd.kind == 1) x ^= 0x80000000u;
+  // negative floats: flip all bits; others: flip the sign bit
+  if (cd.kind == 2) x ^= (uint32_t)((int32_t)x >> 31) | 0x80000000u;
+  if (cd.desc) x = ~x;
+  return x;
+}
+template <> __host__ __device__ __forceinline__ uint32_t decode<4>(uint32_t x, Codec cd) {
+  if (cd.desc) x = ~x;
+  if (cd.kind == 1) x ^= 0x80000000u;
+  if (cd.kind == 2) x ^= (uint32_t)((int32_t)~x >> 31) | 0x80000000u;
+  return x;
+}
+template <> __host__ __device__ __forceinline__ uint64_t encode<8>(uint64_t x, Codec cd) {
+  if (cd.kind == 1) x ^= 0x8000000000000000ull;
+  if (cd.kind == 2) x ^= (uint64_t)((int64_t)x >> 63) | 0x8000000000000000ull;
+  if (cd.desc) x = ~x;
+  return x;
+}
+template <> __host__ __device__ __forceinline__ uint64_t decode<8>(uint64_t x, Codec cd) {
+  if (cd.desc) x = ~x;
+  if (cd.kind == 1) x ^= 0x8000000000000000ull;
+  if (cd.kind == 2) x ^= (uint64_t)((int64_t)~x >> 63) | 0x8000000000000000ull;
+  return x;
+}
+template <> __host__ __device__ __forceinline__ U128 encode<16>(U128 x, Codec cd) {
+  if (cd.kind == 3) x = U128{x.hi, x.lo};   // memory {key, value}: key becomes hi
+  if (cd.desc) x = U128{~x.lo, ~x.hi};
+  return x;
+}
+template <> __host__ __device__ __forceinline__ U128 decode<16>(U128 x, Codec cd) {
+  if (cd.desc) x = U128{~x.lo, ~x.hi};
+  if (cd.kind == 3) x = U128{x.hi, x.lo};
+  return x;
+}
+
+// ---------------------------------------------------------------------------
+// Global memory access for data written by other thread blocks of the same
+// launch: go through L2 (ld.global.cg), never a possibly stale L1 line.
+// ---------------------------------------------------------------------------
+template <int KB> __device__ __forceinline__ typename KT<KB>::Code load_cg(const void *base, uint64_t i);
+template <> __device__ __forceinline__ uint32_t load_cg<2>(const void *b, uint64_t i) {
+  return __ldcg((const unsigned short *)b + i);
+}
+template <> __device__ __forceinline__ uint32_t load_cg<4>(const void *b, uint64_t i) {
+  return __ldcg((const unsigned int *)b + i);
+}
+template <> __device__ __forceinline__ uint64_t load_cg<8>(const void *b, uint64_t i) {
+  return __ldcg((const unsigned long long *)b + i);
+}
+template <> __device__ __forceinline__ U128 load_cg<16>(const void *b, uint64_t i) {
+  ulonglong2 v = __ldcg((const ulonglong2 *)b + i);
+  return U128{v.x, v.y};
+}
+
+template <int KB> __device__ __forceinline__ void store_key(void *base, uint64_t i, typename KT<KB>::Code c);
+template <> __device__ __forceinline__ void store_key<2>(void *b, uint64_t i, uint32_t c) { ((uint16_t *)b)[i] = (uint16_t)c; }
+template <> __device__ __forceinline__ void store_key<4>(void *b, uint64_t i, uint32_t c) { ((uint32_t *)b)[i] = c; }
+template <> __device__ __forceinline__ void store_key<8>(void *b, uint64_t i, uint64_t c) { ((uint64_t *)b)[i] = c; }
+template <> __device__ __forceinline__ void store_key<16>(void *b, uint64_t i, U128 c) {
+  ((ulonglong2 *)b)[i] = make_ulonglong2(c.lo, c.hi);
+}
+
+// ---------------------------------------------------------------------------
+// PTX memory-model helpers (gpu scope).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t ld_acquire(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_relaxed(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed32(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"((unsigned long long)v) : "memory");
+}
+__device__ __forceinline__ void st_release(unsigned long long *p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"((unsigned long long)v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copy (cp.async.bulk) global -> shared with an mbarrier that
+// counts the transferred bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void *smem_dst, const void *gsrc, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Orders this thread's generic-proxy accesses before later async-proxy (TMA)
+// accesses, for global and shared memory.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// Workspace layout (device memory, owned by the caller or by the library).
+// ---------------------------------------------------------------------------
+
+// Counters and status shared by every kernel of one sort call.
+struct Header {
+  unsigned long long head;        // next work-queue ticket to claim
+  unsigned long long tail;        // next free work-queue slot
+  unsigned long long remaining;   // keys still owned by live partition ranges
+  unsigned long long nseg;        // segment descriptors allocated
+  unsigned long long n_leaf_warp, n_leaf_block, n_fb;
+  unsigned long long cur_leaf_warp, cur_leaf_block;
+  unsigned long long bar_count, bar_gen;   // grid barrier of the merge fallback
+  unsigned long long abort;       // set with the first error: every wait gives up
+  unsigned long long error;       // first vq_status raised on the device
+  // statistics
+  unsigned long long keys_partitioned, tiles, segments;
+  unsigned long long leaves_warp, leaves_block, leaf_keys;
+  unsigned long long equal_ranges, equal_keys, degenerate;
+  unsigned long long fallback_ranges, fallback_keys, max_depth;
+  unsigned long long pad[7];
+};
+static_assert(sizeof(Header) % 64 == 0, "header size");
+
+// One range being partitioned (a node of the Quicksort recursion).
+struct SegDesc {
+  unsigned long long begin, end;    // key indices [begin, end)
+  unsigned long long piv_lo, piv_hi;// pivot code (piv_hi only for 16-byte keys)
+  unsigned int q0;                  // queue slot of tile 0 (= look-back status slot)
+  unsigned int ntiles;
+  unsigned int depth;               // partition levels above this range
+  unsigned int flags;               // SEG_* bits
+  unsigned int tiles_done;          // tiles finished (atomic)
+  unsigned int has_lt;              // some key < pivot was seen (atomic)
+  unsigned int depth_limit;         // bound of its root range
+  unsigned int pad;
+};
+static_assert(sizeof(SegDesc) == 64, "segment descriptor size");
+
+enum : unsigned int {
+  SEG_PARITY = 1u,   // keys live in the alternate buffer (else the user buffer)
+  SEG_RAW = 2u,      // keys are still in input form (root ranges)
+  SEG_EXCL = 4u,     // pivot is one below a repeated maximum: right side all equal
+};
+
+// A range handed to the leaf or fallback kernels.
+struct LeafEntry {
+  unsigned long long begin;
+  unsigned int len;
+  unsigned int flags;   // SEG_PARITY, SEG_RAW, LEAF_COPY
+};
+enum : unsigned int { LEAF_COPY = 8u };   // all keys equal: decode and copy only
+
+// Work-queue item: bit 63 valid, bits 32..62 segment id, bits 0..31 tile.
+constexpr unsigned long long ITEM_VALID = 1ull << 63;
+// Look-back status word: bits 62..63 flag, bits 0..61 count of left keys.
+constexpr unsigned long long ST_AGG = 1ull << 62;
+constexpr unsigned long long ST_PFX = 2ull << 62;
+constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
+
+// Warp leaves handle ranges up to this many keys (32 lanes x 16 keys).
+constexpr unsigned WARP_LEAF_MAX = 512;
+// Keys in the pivot sample (Sec. 2.2: 64-byte chunks; here 256 keys).
+constexpr unsigned SAMPLE = 256;
+
+enum : unsigned int {
+  MODE_SORT = 0,
+  MODE_PARTITION = 1,   // one partition only: input raw, output decoded
+};
+
+// Everything a kernel needs, passed by value.
+struct SortArgs {
+  void *keys;                 // user buffer (parity 0)
+  void *alt;                  // alternate buffer (parity 1)
+  Header *hdr;
+  SegDesc *segs;
+  unsigned long long *items;
+  unsigned long long *status;
+  LeafEntry *leaf_warp, *leaf_block, *fb;
+  const unsigned long long *offsets;   // CSR offsets or null (one segment)
+  unsigned long long n_total;
+  unsigned long long num_segments;
+  unsigned long long *out_left;        // MODE_PARTITION result
+  unsigned long long seed;
+  unsigned int cap_q, cap_segs, cap_leaf_warp, cap_leaf_block, cap_fb;
+  unsigned int tile_keys;              // keys per partition tile
+  unsigned int leaf_cutoff;            // ranges <= this go to the leaf kernels
+  int depth_override;                  // < 0: 2*floor(log2 m)+4
+  unsigned int spin_limit;
+  unsigned int mode;
+  unsigned int test_stall;
+  Codec codec;
+  U128 pivot;                          // MODE_PARTITION pivot code
+};
+
+__host__ __device__ __forceinline__ unsigned floor_log2_u64(unsigned long long x) {
+  unsigned r = 0;
+  while (x > 1) { x >>= 1; ++r; }
+  return r;
+}
+
+// Per-range seed of the SFC64 sampling stream: SplitMix64 finaliser of the
+// sort seed, the range start and the depth.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+__host__ __device__ __forceinline__ uint64_t range_seed(uint64_t seed, uint64_t begin, uint32_t depth) {
+  return mix64(seed ^ mix64(begin * 0x9E3779B97F4A7C15ull + depth));
+}
+
+// Raises a device-side error (first one wins) and tells every wait to stop.
+__device__ __forceinline__ void raise_error(const SortArgs &a, unsigned code) {
+  atomicCAS(&a.hdr->error, 0ull, (unsigned long long)code);
+  st_release(&a.hdr->abort, 1);
+}
+
+__device__ __forceinline__ bool aborted(const SortArgs &a) { return ld_relaxed(&a.hdr->abort) != 0; }
+
+}  // namespace vq

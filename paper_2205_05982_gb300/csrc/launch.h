@@ -1,0 +1,46 @@
+// Launch interface between the host driver (vqsort.cu) and the kernel
+// translation units. Every function enqueues on `stream` and returns the
+// CUDA error of the launch.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace vq {
+
+// Partition kernel geometry: 256 threads, 8 chunks of 16 bytes per thread.
+constexpr int PART_NT = 256;
+constexpr int PART_CPT = 8;
+constexpr int PART_WINDOW = PART_NT * PART_CPT * 16;   // bytes of one tile window
+constexpr int PART_SMEM = PART_WINDOW + 64;            // + staging slack
+// Tile keys: the tile plus its 16-byte misalignment fits the window.
+__host__ __device__ constexpr unsigned part_tile_keys(int kb) { return (PART_WINDOW - 16) / kb; }
+
+constexpr int LEAF_NT = 1024;       // threads of the block leaf kernel
+constexpr int FB_NT = 256;          // threads of the merge fallback kernel
+constexpr int FB_R = 8;             // keys per thread in its chunk sort
+constexpr int FB_CHUNK = FB_NT * FB_R;
+
+// Default and largest block-leaf cutoff (keys) per key size.
+__host__ constexpr unsigned default_leaf_cutoff(int kb) {
+  return kb == 2 ? 16384u : kb == 4 ? 16384u : kb == 8 ? 8192u : 4096u;
+}
+__host__ constexpr unsigned max_leaf_cutoff(int kb) {
+  return kb <= 8 ? 16384u : 4096u;   // 16-byte keys: at most 4 per thread in registers
+}
+__host__ constexpr unsigned code_bytes(int kb) { return kb == 2 ? 4u : (unsigned)kb; }
+__host__ constexpr size_t leaf_block_smem(int kb, unsigned cutoff) {
+  return (size_t)(cutoff + cutoff / 32) * code_bytes(kb);
+}
+
+cudaError_t launch_prep(const SortArgs &a, cudaStream_t s);
+cudaError_t launch_seed(int kb, const SortArgs &a, cudaStream_t s);
+cudaError_t launch_partition(int kb, const SortArgs &a, cudaStream_t s);
+cudaError_t launch_choose_pivot(int kb, const SortArgs &a, const void *keys, unsigned long long n,
+                                unsigned long long seed, void *out, cudaStream_t s);
+cudaError_t launch_leaf_warp(int kb, const SortArgs &a, cudaStream_t s);
+cudaError_t launch_leaf_block(int kb, const SortArgs &a, cudaStream_t s);
+cudaError_t launch_fallback(int kb, const SortArgs &a, cudaStream_t s);
+
+}  // namespace vq

@@ -1,0 +1,197 @@
+// Base case of the recursion (Sec. 2.3): ranges of at most the leaf cutoff
+// are sorted by transpose-free sorting networks (Sec. 3) and written, in
+// input form, straight into the user's buffer.
+//
+//   - k_leaf_warp: one warp per range of <= 512 keys; each lane holds R keys
+//     (R = 1..16, the smallest that fits), padded with the all-ones code,
+//     which is the last value in sort order (Sec. 2.3 padding rule).
+//   - k_leaf_block: 1024 threads per range of up to the cutoff (16K keys);
+//     cross-warp merge steps exchange registers through shared memory, and
+//     the sorted keys are staged in shared memory for coalesced stores.
+//     Ranges flagged all-equal are only decoded and copied.
+#include "launch.h"
+#include "sortnet.cuh"
+
+namespace vq {
+
+namespace {
+
+template <int KB> __device__ __forceinline__ typename KT<KB>::Code load_key(const void *b, uint64_t i) {
+  if constexpr (KB == 2) return ((const uint16_t *)b)[i];
+  else if constexpr (KB == 4) return ((const uint32_t *)b)[i];
+  else if constexpr (KB == 8) return ((const uint64_t *)b)[i];
+  else {
+    const ulonglong2 v = ((const ulonglong2 *)b)[i];
+    return U128{v.x, v.y};
+  }
+}
+
+template <int KB, int R>
+__device__ __forceinline__ void warp_leaf(const SortArgs &a, const void *src, uint64_t b, unsigned len, bool raw,
+                                          unsigned lane) {
+  using C = typename KT<KB>::Code;
+  C k[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const unsigned j = r * 32 + lane;
+    if (j < len) {
+      C c = load_key<KB>(src, b + j);
+      k[r] = raw ? encode<KB>(c, a.codec) : c;
+    } else {
+      k[r] = KT<KB>::max_code();
+    }
+  }
+  warp_sort<C, R>(k, lane);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const unsigned i = lane * R + r;
+    if (i < len) store_key<KB>(a.keys, b + i, decode<KB>(k[r], a.codec));
+  }
+}
+
+template <int KB> __global__ void __launch_bounds__(256) k_leaf_warp(SortArgs a) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned long long n = a.hdr->n_leaf_warp;
+  if (a.hdr->abort) return;
+  for (;;) {
+    unsigned long long idx = 0;
+    if (lane == 0) idx = atomicAdd(&a.hdr->cur_leaf_warp, 1ull);
+    idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+    if (idx >= n) break;
+    const LeafEntry le = a.leaf_warp[idx];
+    const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
+    const bool raw = le.flags & SEG_RAW;
+    const unsigned len = le.len;
+    if (len <= 32) warp_leaf<KB, 1>(a, src, le.begin, len, raw, lane);
+    else if (len <= 64) warp_leaf<KB, 2>(a, src, le.begin, len, raw, lane);
+    else if (len <= 128) warp_leaf<KB, 4>(a, src, le.begin, len, raw, lane);
+    else if (len <= 256) warp_leaf<KB, 8>(a, src, le.begin, len, raw, lane);
+    else warp_leaf<KB, 16>(a, src, le.begin, len, raw, lane);
+  }
+}
+
+template <int KB, int R>
+__device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, uint64_t b, unsigned len, bool raw,
+                                           typename KT<KB>::Code *sx) {
+  using C = typename KT<KB>::Code;
+  constexpr int NT = LEAF_NT;
+  const unsigned t = threadIdx.x;
+  C k[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const unsigned j = r * NT + t;
+    if (j < len) {
+      C c = load_key<KB>(src, b + j);
+      k[r] = raw ? encode<KB>(c, a.codec) : c;
+    } else {
+      k[r] = KT<KB>::max_code();
+    }
+  }
+  group_sort<C, R, NT>(k, t, sx);
+  // stage in shared memory (one pad slot per 32 keys) for coalesced stores
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const unsigned i = t * R + r;
+    sx[i + (i >> 5)] = k[r];
+  }
+  __syncthreads();
+  for (unsigned j = t; j < len; j += NT) store_key<KB>(a.keys, b + j, decode<KB>(sx[j + (j >> 5)], a.codec));
+  __syncthreads();
+}
+
+template <int KB> __global__ void __launch_bounds__(LEAF_NT, 1) k_leaf_block(SortArgs a) {
+  using C = typename KT<KB>::Code;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_idx;
+  C *sx = (C *)smem;
+  const unsigned long long n = a.hdr->n_leaf_block;
+  if (a.hdr->abort) return;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(&a.hdr->cur_leaf_block, 1ull);
+    __syncthreads();
+    const unsigned long long idx = s_idx;
+    __syncthreads();
+    if (idx >= n) break;
+    const LeafEntry le = a.leaf_block[idx];
+    const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
+    const bool raw = le.flags & SEG_RAW;
+    const unsigned len = le.len;
+    if (le.flags & LEAF_COPY) {
+      for (unsigned j = threadIdx.x; j < len; j += LEAF_NT) {
+        const C c = load_key<KB>(src, le.begin + j);
+        store_key<KB>(a.keys, le.begin + j, decode<KB>(raw ? encode<KB>(c, a.codec) : c, a.codec));
+      }
+      continue;
+    }
+    if (len <= 1024) block_leaf<KB, 1>(a, src, le.begin, len, raw, sx);
+    else if (len <= 2048) block_leaf<KB, 2>(a, src, le.begin, len, raw, sx);
+    else if (len <= 4096) block_leaf<KB, 4>(a, src, le.begin, len, raw, sx);
+    else if constexpr (KB <= 8) {
+      if (len <= 8192) block_leaf<KB, 8>(a, src, le.begin, len, raw, sx);
+      else block_leaf<KB, 16>(a, src, le.begin, len, raw, sx);
+    }
+  }
+}
+
+template <int KB> int leaf_block_grid(size_t smem) {
+  static int grid = 0;
+  static size_t last = 0;
+  if (!grid || last != smem) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_leaf_block<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)leaf_block_smem(KB, max_leaf_cutoff(KB)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_leaf_block<KB>, LEAF_NT, smem);
+    grid = sms * (per > 0 ? per : 1);
+    last = smem;
+  }
+  return grid;
+}
+
+template <int KB> int leaf_warp_grid() {
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_leaf_warp<KB>, 256, 0);
+    grid = sms * (per > 0 ? per : 1);
+  }
+  return grid;
+}
+
+template <int KB> cudaError_t leaf_block_impl(const SortArgs &a, cudaStream_t s) {
+  const size_t smem = leaf_block_smem(KB, a.leaf_cutoff < 1024 ? 1024 : a.leaf_cutoff);
+  k_leaf_block<KB><<<leaf_block_grid<KB>(smem), LEAF_NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int KB> cudaError_t leaf_warp_impl(const SortArgs &a, cudaStream_t s) {
+  k_leaf_warp<KB><<<leaf_warp_grid<KB>(), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_leaf_warp(int kb, const SortArgs &a, cudaStream_t s) {
+  switch (kb) {
+    case 2: return leaf_warp_impl<2>(a, s);
+    case 4: return leaf_warp_impl<4>(a, s);
+    case 8: return leaf_warp_impl<8>(a, s);
+    case 16: return leaf_warp_impl<16>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_leaf_block(int kb, const SortArgs &a, cudaStream_t s) {
+  switch (kb) {
+    case 2: return leaf_block_impl<2>(a, s);
+    case 4: return leaf_block_impl<4>(a, s);
+    case 8: return leaf_block_impl<8>(a, s);
+    case 16: return leaf_block_impl<16>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace vq

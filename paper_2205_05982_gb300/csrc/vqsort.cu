@@ -1,0 +1,599 @@
+// Host driver of libvqsort.so: argument checks, workspace layout, the fixed
+// launch sequence of one sort, options, statistics and per-kernel timing.
+// Everything data-dependent runs on the device; the host never waits inside
+// a sort call.
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "launch.h"
+#include "networks.h"
+#include "../../include/vqsort.h"
+
+using namespace vq;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Key types.
+// ---------------------------------------------------------------------------
+int key_bytes(vq_dtype dt) {
+  switch (dt) {
+    case VQ_I16: case VQ_U16: return 2;
+    case VQ_I32: case VQ_U32: case VQ_F32: return 4;
+    case VQ_I64: case VQ_U64: case VQ_F64: return 8;
+    case VQ_U128: case VQ_KV64: return 16;
+  }
+  return 0;
+}
+
+Codec codec_of(vq_dtype dt, int ascending) {
+  Codec c;
+  c.desc = ascending ? 0 : 1;
+  switch (dt) {
+    case VQ_I16: case VQ_I32: case VQ_I64: c.kind = 1; break;
+    case VQ_F32: case VQ_F64: c.kind = 2; break;
+    case VQ_KV64: c.kind = 3; break;
+    default: c.kind = 0; break;
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Options.
+// ---------------------------------------------------------------------------
+std::mutex g_mu;
+int64_t g_depth_limit = -1;
+int64_t g_leaf_cutoff = 0;
+int64_t g_seed = 0x22050598;
+int64_t g_spin_limit = 1 << 22;
+int64_t g_test_stall = 0;
+
+unsigned leaf_cutoff_for(int kb) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_leaf_cutoff > 0) return (unsigned)g_leaf_cutoff < max_leaf_cutoff(kb) ? (unsigned)g_leaf_cutoff
+                                                                             : max_leaf_cutoff(kb);
+  return default_leaf_cutoff(kb);
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout.
+// ---------------------------------------------------------------------------
+struct Layout {
+  size_t hdr, segs, items, status, lw, lb, fb, alt, total;
+  unsigned cap_q, cap_segs, cap_lw, cap_lb, cap_fb;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_limit, bool with_alt) {
+  const uint64_t T = part_tile_keys(kb);
+  const uint64_t lg = floor_log2_u64(n < 2 ? 2 : n);
+  uint64_t levels = 2 * lg + 4;
+  if (depth_limit >= 0 && (uint64_t)depth_limit > levels) levels = (uint64_t)depth_limit;
+  levels += 2;
+  const uint64_t per_level = n / (C + 1ull) + 1;
+  Layout L{};
+  const uint64_t cap_segs = (levels + 1) * per_level + 16;
+  const uint64_t cap_q = (levels + 1) * ((n + T - 1) / T + per_level) + 16;
+  const uint64_t cap_lw = 2 * cap_segs + S + 16;
+  const uint64_t cap_lb = n / 512 + n / C + 2 * cap_segs + S + 16;
+  const uint64_t cap_fb = n / (C + 1ull) + S + 16;
+  L.cap_segs = (unsigned)cap_segs;
+  L.cap_q = (unsigned)cap_q;
+  L.cap_lw = (unsigned)cap_lw;
+  L.cap_lb = (unsigned)cap_lb;
+  L.cap_fb = (unsigned)cap_fb;
+  size_t off = 0;
+  L.hdr = off; off = align256(off + sizeof(Header));
+  L.segs = off; off = align256(off + cap_segs * sizeof(SegDesc));
+  L.items = off; off = align256(off + cap_q * 8);
+  L.status = off; off = align256(off + cap_q * 8);
+  L.lw = off; off = align256(off + cap_lw * sizeof(LeafEntry));
+  L.lb = off; off = align256(off + cap_lb * sizeof(LeafEntry));
+  L.fb = off; off = align256(off + cap_fb * sizeof(LeafEntry));
+  L.alt = off;
+  if (with_alt) off = align256(off + n * (uint64_t)kb);
+  L.total = off;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// Library-owned workspaces, one per (device, stream).
+// ---------------------------------------------------------------------------
+struct OwnedWs {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+std::map<std::pair<int, cudaStream_t>, OwnedWs> g_ws;
+
+vq_status owned_ws(cudaStream_t s, size_t need, void **ptr, size_t *bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VQ_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  OwnedWs &w = g_ws[{dev, s}];
+  if (w.bytes < need) {
+    if (w.ptr) {
+      if (cudaStreamSynchronize(s) != cudaSuccess) return VQ_ERR_CUDA;
+      cudaFree(w.ptr);
+      w.ptr = nullptr;
+      w.bytes = 0;
+    }
+    const size_t grow = need + need / 8;
+    if (cudaMalloc(&w.ptr, grow) != cudaSuccess) {
+      cudaGetLastError();
+      return VQ_ERR_NOMEM;
+    }
+    w.bytes = grow;
+  }
+  *ptr = w.ptr;
+  *bytes = w.bytes;
+  return VQ_OK;
+}
+
+const void *lookup_ws(cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_ws.find({dev, s});
+  return it == g_ws.end() ? nullptr : it->second.ptr;
+}
+
+// ---------------------------------------------------------------------------
+// Per-kernel timing.
+// ---------------------------------------------------------------------------
+struct ProfEntry {
+  double ms = 0;
+  uint64_t launches = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+bool g_prof = false;
+std::map<std::string, ProfEntry> g_prof_tab;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+template <class F> cudaError_t timed(const char *name, cudaStream_t s, F &&f) {
+  bool prof;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    prof = g_prof;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (prof) cudaStreamIsCapturing(s, &cs);
+  if (!prof || cs != cudaStreamCaptureStatusNone) return f();
+  cudaEvent_t e0, e1;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    e0 = take_event();
+    e1 = take_event();
+  }
+  cudaEventRecord(e0, s);
+  const cudaError_t err = f();
+  cudaEventRecord(e1, s);
+  std::lock_guard<std::mutex> lk(g_mu);
+  ProfEntry &p = g_prof_tab[name];
+  p.pending.push_back({e0, e1});
+  p.launches++;
+  return err;
+}
+
+// ---------------------------------------------------------------------------
+// Device check (compute capability 10.3).
+// ---------------------------------------------------------------------------
+vq_status check_device() {
+  static int ok_dev = -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VQ_ERR_CUDA;
+  if (ok_dev == dev) return VQ_OK;
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+    return VQ_ERR_CUDA;
+  if (major != 10 || minor != 3) return VQ_ERR_UNSUPPORTED;
+  ok_dev = dev;
+  return VQ_OK;
+}
+
+vq_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VQ_OK : VQ_ERR_CUDA; }
+
+// ---------------------------------------------------------------------------
+// One sort (or one standalone partition) on a workspace.
+// ---------------------------------------------------------------------------
+struct Job {
+  vq_dtype dt;
+  void *keys;
+  void *alt_given;                 // MODE_PARTITION: the output buffer
+  uint64_t n;
+  const uint64_t *offsets;
+  uint64_t num_segments;
+  int ascending;
+  unsigned mode;
+  const void *pivot_host;
+  uint64_t *out_left;
+};
+
+vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
+  const int kb = key_bytes(j.dt);
+  const unsigned C = leaf_cutoff_for(kb);
+  int64_t depth_limit, seed, spin, stall;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    depth_limit = g_depth_limit;
+    seed = g_seed;
+    spin = g_spin_limit;
+    stall = g_test_stall;
+  }
+  const bool with_alt = j.mode == MODE_SORT;
+  const Layout L = make_layout(kb, j.n, j.num_segments, C, depth_limit, with_alt);
+  if (!ws || ws_bytes < L.total) return VQ_ERR_NOMEM;
+  if ((uintptr_t)ws & 255) return VQ_ERR_INVALID;
+  unsigned char *w = (unsigned char *)ws;
+  SortArgs a{};
+  a.keys = j.keys;
+  a.alt = with_alt ? (void *)(w + L.alt) : j.alt_given;
+  a.hdr = (Header *)(w + L.hdr);
+  a.segs = (SegDesc *)(w + L.segs);
+  a.items = (unsigned long long *)(w + L.items);
+  a.status = (unsigned long long *)(w + L.status);
+  a.leaf_warp = (LeafEntry *)(w + L.lw);
+  a.leaf_block = (LeafEntry *)(w + L.lb);
+  a.fb = (LeafEntry *)(w + L.fb);
+  a.offsets = (const unsigned long long *)j.offsets;
+  a.n_total = j.n;
+  a.num_segments = j.num_segments;
+  a.out_left = (unsigned long long *)j.out_left;
+  a.seed = (unsigned long long)seed;
+  a.cap_q = L.cap_q;
+  a.cap_segs = L.cap_segs;
+  a.cap_leaf_warp = L.cap_lw;
+  a.cap_leaf_block = L.cap_lb;
+  a.cap_fb = L.cap_fb;
+  a.tile_keys = part_tile_keys(kb);
+  a.leaf_cutoff = C;
+  a.depth_override = (int)depth_limit;
+  a.spin_limit = (unsigned)spin;
+  a.mode = j.mode;
+  a.test_stall = (unsigned)stall;
+  a.codec = codec_of(j.dt, j.ascending);
+  a.pivot = U128{0, 0};
+  if (j.mode == MODE_PARTITION) {
+    // the pivot's code, by the same codec the kernels use
+    switch (kb) {
+      case 2: { uint16_t v; memcpy(&v, j.pivot_host, 2); a.pivot.lo = encode<2>(v, a.codec); break; }
+      case 4: { uint32_t v; memcpy(&v, j.pivot_host, 4); a.pivot.lo = encode<4>(v, a.codec); break; }
+      case 8: { uint64_t v; memcpy(&v, j.pivot_host, 8); a.pivot.lo = encode<8>(v, a.codec); break; }
+      case 16: { U128 v; memcpy(&v, j.pivot_host, 16); a.pivot = encode<16>(v, a.codec); break; }
+    }
+  }
+  cudaError_t e;
+  if ((e = timed("prep", s, [&] { return launch_prep(a, s); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed("seed", s, [&] { return launch_seed(kb, a, s); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed("partition", s, [&] { return launch_partition(kb, a, s); })) != cudaSuccess) return cuda_status(e);
+  if (j.mode == MODE_SORT) {
+    if ((e = timed("leaf_warp", s, [&] { return launch_leaf_warp(kb, a, s); })) != cudaSuccess) return cuda_status(e);
+    if ((e = timed("leaf_block", s, [&] { return launch_leaf_block(kb, a, s); })) != cudaSuccess) return cuda_status(e);
+    if ((e = timed("fallback", s, [&] { return launch_fallback(kb, a, s); })) != cudaSuccess) return cuda_status(e);
+  }
+  return VQ_OK;
+}
+
+vq_status check_keys(vq_dtype dt, const void *p, uint64_t n) {
+  const int kb = key_bytes(dt);
+  if (!kb) return VQ_ERR_INVALID;
+  if (n > 0 && !p) return VQ_ERR_INVALID;
+  if ((uintptr_t)p % kb) return VQ_ERR_INVALID;
+  if (n >= (1ull << 32) - 1) return VQ_ERR_INVALID;   // per-range lengths are 32-bit in leaf lists
+  return VQ_OK;
+}
+
+vq_status sort_common(vq_dtype dt, void *keys, uint64_t n, const uint64_t *offsets, uint64_t S, int asc,
+                      void *ws, size_t ws_bytes, void *stream) {
+  vq_status st = check_keys(dt, keys, n);
+  if (st != VQ_OK) return st;
+  if (offsets == nullptr && n <= 1) return VQ_OK;
+  if (offsets != nullptr && S == 0) return VQ_OK;
+  if ((st = check_device()) != VQ_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!ws) {
+    const int kb = key_bytes(dt);
+    int64_t dl;
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      dl = g_depth_limit;
+    }
+    const Layout L = make_layout(kb, n, offsets ? S : 1, leaf_cutoff_for(kb), dl, true);
+    if ((st = owned_ws(s, L.total, &ws, &ws_bytes)) != VQ_OK) return st;
+  }
+  Job j{dt, keys, nullptr, n, offsets, offsets ? S : 1, asc, MODE_SORT, nullptr, nullptr};
+  return run(j, ws, ws_bytes, s);
+}
+
+// Library-owned resources of the host entry point.
+struct HostCtx {
+  cudaStream_t stream = nullptr;
+  void *dbuf = nullptr;
+  size_t dbytes = 0;
+};
+std::map<int, HostCtx> g_host;
+
+vq_status read_header(const void *ws, void *stream, Header *h) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!ws) ws = lookup_ws(s);
+  if (!ws) return VQ_ERR_INVALID;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return VQ_ERR_CUDA;
+  if (cudaMemcpy(h, ws, sizeof(Header), cudaMemcpyDeviceToHost) != cudaSuccess) return VQ_ERR_CUDA;
+  return VQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vq_status vqsort_sort(vq_dtype dt, void *d_keys, size_t n, int ascending, void *stream) {
+  return sort_common(dt, d_keys, n, nullptr, 1, ascending, nullptr, 0, stream);
+}
+
+vq_status vqsort_sort_kv(void *d_pairs, size_t n, int ascending, void *stream) {
+  return sort_common(VQ_KV64, d_pairs, n, nullptr, 1, ascending, nullptr, 0, stream);
+}
+
+vq_status vqsort_sort_segmented(vq_dtype dt, void *d_keys, size_t n_total, const uint64_t *d_offsets,
+                                size_t num_segments, int ascending, void *stream) {
+  if (!d_offsets && num_segments) return VQ_ERR_INVALID;
+  return sort_common(dt, d_keys, n_total, d_offsets, num_segments, ascending, nullptr, 0, stream);
+}
+
+size_t vqsort_workspace_bytes(vq_dtype dt, size_t n_total, size_t num_segments) {
+  const int kb = key_bytes(dt);
+  if (!kb) return 0;
+  int64_t dl;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    dl = g_depth_limit;
+  }
+  return make_layout(kb, n_total, num_segments ? num_segments : 1, leaf_cutoff_for(kb), dl, true).total;
+}
+
+vq_status vqsort_sort_ws(vq_dtype dt, void *d_keys, size_t n, int ascending, void *d_ws, size_t ws_bytes,
+                         void *stream) {
+  if (!d_ws) return VQ_ERR_INVALID;
+  return sort_common(dt, d_keys, n, nullptr, 1, ascending, d_ws, ws_bytes, stream);
+}
+
+vq_status vqsort_sort_segmented_ws(vq_dtype dt, void *d_keys, size_t n_total, const uint64_t *d_offsets,
+                                   size_t num_segments, int ascending, void *d_ws, size_t ws_bytes,
+                                   void *stream) {
+  if (!d_ws || (!d_offsets && num_segments)) return VQ_ERR_INVALID;
+  return sort_common(dt, d_keys, n_total, d_offsets, num_segments, ascending, d_ws, ws_bytes, stream);
+}
+
+vq_status vqsort_sort_host(vq_dtype dt, void *h_keys, size_t n, int ascending) {
+  vq_status st = check_keys(dt, h_keys, n);
+  if (st != VQ_OK) return st;
+  if (n <= 1) return VQ_OK;
+  if ((st = check_device()) != VQ_OK) return st;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  HostCtx *hc;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    hc = &g_host[dev];
+    if (!hc->stream && cudaStreamCreateWithFlags(&hc->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return VQ_ERR_CUDA;
+  }
+  const size_t bytes = n * (size_t)key_bytes(dt);
+  if (hc->dbytes < bytes) {
+    if (hc->dbuf) cudaFree(hc->dbuf);
+    hc->dbuf = nullptr;
+    hc->dbytes = 0;
+    if (cudaMalloc(&hc->dbuf, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return VQ_ERR_NOMEM;
+    }
+    hc->dbytes = bytes;
+  }
+  if (cudaMemcpyAsync(hc->dbuf, h_keys, bytes, cudaMemcpyHostToDevice, hc->stream) != cudaSuccess)
+    return VQ_ERR_CUDA;
+  if ((st = sort_common(dt, hc->dbuf, n, nullptr, 1, ascending, nullptr, 0, hc->stream)) != VQ_OK) return st;
+  if (cudaMemcpyAsync(h_keys, hc->dbuf, bytes, cudaMemcpyDeviceToHost, hc->stream) != cudaSuccess)
+    return VQ_ERR_CUDA;
+  return vqsort_last_device_status(nullptr, hc->stream);
+}
+
+vq_status vqsort_partition(vq_dtype dt, const void *d_in, void *d_out, size_t n, const void *h_pivot,
+                           int ascending, uint64_t *d_left_count, void *stream) {
+  vq_status st = check_keys(dt, d_in, n);
+  if (st != VQ_OK) return st;
+  if ((st = check_keys(dt, d_out, n)) != VQ_OK) return st;
+  if (!h_pivot || !d_left_count || (n > 0 && d_in == d_out)) return VQ_ERR_INVALID;
+  if ((st = check_device()) != VQ_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int kb = key_bytes(dt);
+  const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb), -1, false);
+  void *ws;
+  size_t wsb;
+  if ((st = owned_ws(s, L.total, &ws, &wsb)) != VQ_OK) return st;
+  Job j{dt, const_cast<void *>(d_in), d_out, n, nullptr, 1, ascending, MODE_PARTITION, h_pivot, d_left_count};
+  return run(j, ws, wsb, s);
+}
+
+vq_status vqsort_choose_pivot(vq_dtype dt, const void *d_keys, size_t n, uint64_t seed, int ascending,
+                              void *d_pivot_out, void *stream) {
+  vq_status st = check_keys(dt, d_keys, n);
+  if (st != VQ_OK) return st;
+  if (n < 1024 || !d_pivot_out) return VQ_ERR_INVALID;
+  if ((st = check_device()) != VQ_OK) return st;
+  SortArgs a{};
+  a.codec = codec_of(dt, ascending);
+  cudaStream_t s = (cudaStream_t)stream;
+  return cuda_status(timed("choose_pivot", s, [&] {
+    return launch_choose_pivot(key_bytes(dt), a, d_keys, n, seed, d_pivot_out, s);
+  }));
+}
+
+vq_status vqsort_last_device_status(const void *d_ws, void *stream) {
+  Header h;
+  const vq_status st = read_header(d_ws, stream, &h);
+  if (st != VQ_OK) return st;
+  return (vq_status)h.error;
+}
+
+vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out) {
+  if (!out) return VQ_ERR_INVALID;
+  Header h;
+  const vq_status st = read_header(d_ws, stream, &h);
+  if (st != VQ_OK) return st;
+  out->keys_partitioned = h.keys_partitioned;
+  out->tiles = h.tiles;
+  out->segments = h.segments;
+  out->leaves_warp = h.leaves_warp;
+  out->leaves_block = h.leaves_block;
+  out->leaf_keys = h.leaf_keys;
+  out->equal_ranges = h.equal_ranges;
+  out->equal_keys = h.equal_keys;
+  out->degenerate = h.degenerate;
+  out->fallback_ranges = h.fallback_ranges;
+  out->fallback_keys = h.fallback_keys;
+  out->max_depth = h.max_depth;
+  out->device_status = h.error;
+  return VQ_OK;
+}
+
+const char *vqsort_status_string(vq_status s) {
+  switch (s) {
+    case VQ_OK: return "ok";
+    case VQ_ERR_INVALID: return "invalid argument";
+    case VQ_ERR_UNSUPPORTED: return "unsupported device (needs compute capability 10.3)";
+    case VQ_ERR_NOMEM: return "workspace too small or allocation failed";
+    case VQ_ERR_CUDA: return "CUDA runtime error";
+    case VQ_ERR_TIMEOUT: return "a bounded device-side wait ran out";
+    case VQ_ERR_INTERNAL: return "device-side capacity overflow";
+  }
+  return "unknown status";
+}
+
+vq_status vqsort_set_option(vq_option opt, int64_t value) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  switch (opt) {
+    case VQ_OPT_DEPTH_LIMIT:
+      if (value < -1 || value > 1000) return VQ_ERR_INVALID;
+      g_depth_limit = value;
+      return VQ_OK;
+    case VQ_OPT_LEAF_CUTOFF:
+      // applies to every key size; 16-byte keys clamp it to 4096
+      if (value != 0 && (value < 1024 || value > 16384 || (value & (value - 1)))) return VQ_ERR_INVALID;
+      g_leaf_cutoff = value;
+      return VQ_OK;
+    case VQ_OPT_SEED: g_seed = value; return VQ_OK;
+    case VQ_OPT_SPIN_LIMIT:
+      if (value < 1 || value > (1ll << 30)) return VQ_ERR_INVALID;
+      g_spin_limit = value;
+      return VQ_OK;
+    case VQ_OPT_TEST_STALL: g_test_stall = value ? 1 : 0; return VQ_OK;
+  }
+  return VQ_ERR_INVALID;
+}
+
+int64_t vqsort_get_option(vq_option opt) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  switch (opt) {
+    case VQ_OPT_DEPTH_LIMIT: return g_depth_limit;
+    case VQ_OPT_LEAF_CUTOFF: return g_leaf_cutoff;
+    case VQ_OPT_SEED: return g_seed;
+    case VQ_OPT_SPIN_LIMIT: return g_spin_limit;
+    case VQ_OPT_TEST_STALL: return g_test_stall;
+  }
+  return -1;
+}
+
+vq_status vqsort_merge_schedule(unsigned run_len, unsigned keys_per_thread, unsigned *pairs_out, size_t max_pairs,
+                                size_t *n_pairs) {
+  const unsigned L = run_len, R = keys_per_thread;
+  if (!n_pairs || L == 0 || R == 0 || (L & (L - 1)) || (R & (R - 1)) || R > L) return VQ_ERR_INVALID;
+  size_t k = 0;
+  const unsigned steps = vq_merge_steps(L);
+  for (unsigned s = 0; s < steps; ++s) {
+    const VqMergeStep m = vq_merge_step(L, R, s);
+    for (unsigned t = 0; t < 2 * L / R; ++t) {
+      for (unsigned r = 0; r < R; ++r) {
+        unsigned pt, pr;
+        if (m.lane_xor) {
+          pt = t ^ m.lane_xor;
+          pr = m.reverse ? R - 1 - r : r;
+        } else {
+          pt = t;
+          pr = r ^ m.reg_xor;
+        }
+        const unsigned i = t * R + r, j = pt * R + pr;
+        if (i < j) {
+          if (pairs_out && k < max_pairs) {
+            pairs_out[2 * k] = i;
+            pairs_out[2 * k + 1] = j;
+          }
+          ++k;
+        }
+      }
+    }
+  }
+  *n_pairs = k;
+  return VQ_OK;
+}
+
+vq_status vqsort_profile_enable(int enable) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_prof = enable != 0;
+  return VQ_OK;
+}
+
+vq_status vqsort_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto &kv : g_prof_tab)
+    for (auto &pe : kv.second.pending) {
+      cudaEventSynchronize(pe.second);
+      g_event_pool.push_back(pe.first);
+      g_event_pool.push_back(pe.second);
+    }
+  g_prof_tab.clear();
+  return VQ_OK;
+}
+
+vq_status vqsort_profile_read(const char **names, double *ms, uint64_t *launches, size_t max, size_t *count) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  size_t k = 0;
+  for (auto &kv : g_prof_tab) {
+    ProfEntry &p = kv.second;
+    for (auto &pe : p.pending) {
+      if (cudaEventSynchronize(pe.second) != cudaSuccess) return VQ_ERR_CUDA;
+      float t = 0;
+      cudaEventElapsedTime(&t, pe.first, pe.second);
+      p.ms += t;
+      g_event_pool.push_back(pe.first);
+      g_event_pool.push_back(pe.second);
+    }
+    p.pending.clear();
+    if (k < max) {
+      if (names) names[k] = kv.first.c_str();
+      if (ms) ms[k] = p.ms;
+      if (launches) launches[k] = p.launches;
+    }
+    ++k;
+  }
+  if (count) *count = k;
+  return VQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA sort through the C ABI must equal the CPU oracle
+byte for byte (the sorted output is unique, so bit-exact is the bar)."""
+import numpy as np
+import pytest
+
+from paper_2205_05982_gb300 import inputs
+from tests.gpu_util import first_mismatch, same_bits, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+ALL = ("i16", "u16", "i32", "u32", "f32", "i64", "u64", "f64", "u128", "kv64")
+# sizes around the warp-leaf limit (512), block-leaf cutoffs (4K/8K/16K),
+# partition tile sizes (2047/4094/8188/16376 keys) and ragged tails
+SIZES = (0, 1, 2, 33, 257, 513, 1025, 4097, 8193, 16385, 40001, 262147)
+
+
+def make(dtype, n, dist, seed=1):
+    if dtype == "kv64" and dist == "uniform":
+        return inputs.kv_pairs(n, seed=seed)
+    return inputs.make(dtype, n, dist, seed=seed, specials=True)
+
+
+def check_sort(vq, oracle_mod, dtype, a, ascending):
+    want = oracle_mod.sort(a, dtype, ascending)
+    t = to_dev(a, dtype)
+    vq.sort_(t, dtype, descending=not ascending)
+    got = to_host(t, dtype, a)
+    assert vq.last_device_status() == 0
+    if not same_bits(got, want):
+        i, cnt = first_mismatch(got, want)
+        pytest.fail(f"{dtype} n={len(a)} asc={ascending}: {cnt} mismatches, first at {i}")
+
+
+@pytest.mark.parametrize("dtype", ALL)
+@pytest.mark.parametrize("n", SIZES)
+def test_uniform_all_sizes(vq, oracle_mod, dtype, n):
+    a = make(dtype, n, "uniform", seed=n + 3)
+    check_sort(vq, oracle_mod, dtype, a, True)
+    check_sort(vq, oracle_mod, dtype, a, False)
+
+
+@pytest.mark.parametrize("dtype", ALL)
+@pytest.mark.parametrize("dist", ("distinct16", "equal", "sorted", "reverse", "organpipe"))
+@pytest.mark.parametrize("n", (1000, 50001, 400009))
+def test_distributions(vq, oracle_mod, dtype, dist, n):
+    a = make(dtype, n, dist, seed=7)
+    check_sort(vq, oracle_mod, dtype, a, True)
+    check_sort(vq, oracle_mod, dtype, a, False)
+
+
+@pytest.mark.parametrize("dtype", ("u64", "f32", "i16", "kv64"))
+def test_one_million(vq, oracle_mod, dtype):
+    a = make(dtype, 1_000_000, "uniform", seed=11)
+    check_sort(vq, oracle_mod, dtype, a, True)
+
+
+def test_full_size_u64_uniform(vq, oracle_mod):
+    """1e8 uniform u64 keys (the benchmark's workload) against the oracle."""
+    a = inputs.make("u64", 100_000_000, "uniform")
+    check_sort(vq, oracle_mod, "u64", a, True)
+    st = vq.stats()
+    assert st["fallback_ranges"] == 0
+    assert st["max_depth"] <= 2 * 26 + 4
+
+
+@pytest.mark.parametrize("dtype,dist,asc", [("f32", "uniform", False), ("i32", "organpipe", True),
+                                            ("i16", "distinct16", True), ("u64", "reverse", False)])
+def test_full_size_properties(vq, oracle_mod, dtype, dist, asc):
+    """1e8 keys: the output's codes (oracle codec) never decrease and the
+    output is a permutation of the input (equal sorted bit patterns)."""
+    n = 100_000_000
+    a = inputs.make(dtype, n, dist, specials=True)
+    t = to_dev(a, dtype)
+    vq.sort_(t, dtype, descending=not asc)
+    got = to_host(t, dtype, a)
+    assert vq.last_device_status() == 0
+    codes = oracle_mod.encode(got, dtype, asc)
+    assert bool((codes[1:] >= codes[:-1]).all())
+    ut = {2: np.uint16, 4: np.uint32, 8: np.uint64}[a.itemsize]
+    assert np.array_equal(np.sort(got.view(ut)), np.sort(a.view(ut)))
+
+
+@pytest.mark.parametrize("dtype", ("u128", "kv64"))
+def test_wide_keys_c3(vq, oracle_mod, dtype):
+    """2.5e7 u128 keys / kv64 pairs with 10 % duplicated keys (pairing kept)."""
+    n = 25_000_000
+    a = inputs.kv_pairs(n) if dtype == "kv64" else inputs.make("u128", n)
+    check_sort(vq, oracle_mod, dtype, a, True)
+    if dtype == "kv64":
+        t = to_dev(a, dtype)
+        vq.sort_kv_(t)
+        got = to_host(t, dtype, a)
+        idx = got[:, 1].astype(np.int64)
+        assert np.array_equal(got[:, 0], a[idx, 0])
+
+
+@pytest.mark.parametrize("dtype", ("u32", "f32", "u64", "kv64"))
+def test_segmented(vq, oracle_mod, dtype):
+    sizes = inputs.segment_sizes(400, 16, 65536, seed=5)
+    sizes[::37] = 0
+    sizes[1::41] = 1
+    off = inputs.offsets_from_sizes(sizes)
+    n = int(off[-1])
+    a = inputs.kv_pairs(n, seed=5) if dtype == "kv64" else inputs.make(dtype, n, "uniform", seed=5,
+                                                                        specials=True)
+    want = oracle_mod.sort_segmented(a, off, dtype, True)
+    t = to_dev(a, dtype)
+    vq.sort_segmented_(t, off.astype(np.int64), dtype)
+    got = to_host(t, dtype, a)
+    assert vq.last_device_status() == 0
+    assert same_bits(got, want), first_mismatch(got, want)
+
+
+def test_segmented_bad_offsets_reported(vq):
+    import torch
+    t = torch.zeros(100, dtype=torch.int32, device="cuda")
+    vq.sort_segmented_(t, np.array([0, 50, 40, 100]), "u32")
+    assert vq.last_device_status() == 1
+
+
+def test_zero_one_principle_leaves(vq):
+    """All 2**16 0/1 vectors of 16 keys as one segmented batch (warp
+    networks), plus random 0/1 arrays that reach the block networks."""
+    import torch
+    x = np.arange(2 ** 16, dtype=np.uint32)
+    bits = ((x[:, None] >> np.arange(16, dtype=np.uint32)[None, :]) & 1).astype(np.uint32).reshape(-1)
+    off = np.arange(0, bits.size + 1, 16, dtype=np.int64)
+    t = torch.from_numpy(bits.view(np.int32)).cuda()
+    vq.sort_segmented_(t, off, "u32")
+    got = t.cpu().numpy().view(np.uint32).reshape(-1, 16)
+    assert (np.diff(got.astype(np.int64), axis=1) >= 0).all()
+    assert np.array_equal(got.sum(axis=1), bits.reshape(-1, 16).sum(axis=1))
+    rng = np.random.default_rng(0)
+    for n in (600, 3000, 5000, 9000, 16000):
+        b = rng.integers(0, 2, size=n).astype(np.uint64)
+        tt = torch.from_numpy(b.view(np.int64)).cuda()
+        vq.sort_(tt, "u64")
+        g = tt.cpu().numpy().view(np.uint64)
+        assert np.array_equal(g, np.sort(b))
+
+
+def test_back_to_back_sorts_reuse_workspace(vq, oracle_mod):
+    for n, seed in ((300_000, 1), (5_000, 2), (1_000_003, 3), (70_000, 4)):
+        a = inputs.make("u32", n, "uniform", seed=seed)
+        check_sort(vq, oracle_mod, "u32", a, True)
+
+
+def test_explicit_workspace_and_graph_capture(vq, oracle_mod):
+    """The workspace form allocates nothing, so a sort can be captured in a
+    CUDA graph and replayed on new contents of the same buffer."""
+    import torch
+    n = 500_000
+    a1 = inputs.make("u64", n, "uniform", seed=21)
+    a2 = inputs.make("u64", n, "uniform", seed=22)
+    t = to_dev(a1, "u64")
+    ws = vq.alloc_workspace("u64", n)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        vq.sort_ws_(t, ws, "u64")
+    s.synchronize()
+    assert same_bits(to_host(t, "u64", a1), oracle_mod.sort(a1, "u64"))
+    t.copy_(to_dev(a2, "u64"))
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        vq.sort_ws_(t, ws, "u64")
+    for src in (a1, a2):
+        t.copy_(to_dev(src, "u64"))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert same_bits(to_host(t, "u64", src), oracle_mod.sort(src, "u64"))
+
+
+@pytest.mark.parametrize("dtype", ("u32", "i64", "f64", "u128"))
+@pytest.mark.parametrize("limit", (0, 1, 3))
+def test_depth_bound_fallback(vq, oracle_mod, dtype, limit):
+    """Forcing the depth bound low sends ranges to the merge fallback; the
+    result must not change."""
+    vq.set_option("depth_limit", limit)
+    try:
+        for dist in ("uniform", "organpipe", "distinct16"):
+            a = make(dtype, 200_003, dist, seed=9)
+            check_sort(vq, oracle_mod, dtype, a, True)
+            st = vq.stats()
+            assert st["fallback_ranges"] >= 1
+    finally:
+        vq.set_option("depth_limit", -1)
+
+
+@pytest.mark.parametrize("cutoff", (1024, 4096, 16384))
+def test_leaf_cutoff_option(vq, oracle_mod, cutoff):
+    vq.set_option("leaf_cutoff", cutoff)
+    try:
+        for dtype in ("u16", "f32", "u64"):
+            a = make(dtype, 300_001, "uniform", seed=cutoff)
+            check_sort(vq, oracle_mod, dtype, a, False)
+    finally:
+        vq.set_option("leaf_cutoff", 0)
+
+
+def test_bounded_wait_reports_timeout(vq, oracle_mod):
+    """A tile whose count is never published: the next tile's bounded wait
+    runs out, the sort reports VQ_ERR_TIMEOUT, and the next sort is fine."""
+    import torch
+    a = inputs.make("u32", 200_000, "uniform", seed=4)
+    vq.set_option("spin_limit", 1 << 14)
+    vq.set_option("test_stall", 1)
+    try:
+        t = to_dev(a, "u32")
+        vq.sort_(t, "u32")
+        assert vq.last_device_status() == 5
+    finally:
+        vq.set_option("test_stall", 0)
+        vq.set_option("spin_limit", 1 << 22)
+    torch.cuda.synchronize()
+    check_sort(vq, oracle_mod, "u32", a, True)
+
+
+def test_host_entry(vq, oracle_mod):
+    a = inputs.make("f32", 2_000_003, "uniform", seed=31, specials=True)
+    want = oracle_mod.sort(a, "f32", False)
+    b = a.copy()
+    vq.sort_host(b, "f32", descending=True)
+    assert same_bits(b, want)
+
+
+def test_stats_are_consistent(vq):
+    import torch
+    n = 10_000_000
+    a = inputs.make("u64", n, "uniform", seed=2)
+    t = to_dev(a, "u64")
+    vq.sort_(t, "u64")
+    st = vq.stats()
+    assert st["device_status"] == 0
+    assert st["leaf_keys"] + st["equal_keys"] + st["fallback_keys"] == n
+    assert st["keys_partitioned"] >= n            # at least the root level
+    assert st["max_depth"] <= 2 * 23 + 4
+    torch.cuda.synchronize()
