@@ -1,0 +1,325 @@
+"""Benchmark: vqsort on GB300, one JSON line on stdout.
+
+Workload: one array of 1e8 uniform random uint64 keys (full 64-bit range,
+seeded SplitMix64), sorted ascending by the plain path; a step is one full
+sort (all partition levels, leaves, fallback check). Inputs are 800 MB per
+array, larger than L2, and every timed step sorts its own fresh copy, so no
+step sees a cache warmed by the previous one.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--n N_KEYS] [--dtype u64] [--dist uniform]
+
+--impl reference times the CPU oracle (plain scalar Quicksort) on host cores
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2205_05982_gb300 import inputs  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--n", type=int, default=100_000_000)
+    p.add_argument("--dtype", default="u64")
+    p.add_argument("--dist", default="uniform")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload(args):
+    return {
+        "workload": f"{args.n:.0e} {args.dist} {args.dtype} keys, one array, ascending "
+                    "(plain partition + sorting-network Quicksort)",
+        "n_keys": args.n, "key_type": args.dtype, "distribution": args.dist,
+        "seed": inputs.DEFAULT_SEED,
+        "l2": "inputs larger than L2 (one fresh array per timed step)",
+    }
+
+
+def make_input(args):
+    if args.dtype == "kv64":
+        return inputs.kv_pairs(args.n)
+    return inputs.make(args.dtype, args.n, args.dist, specials=args.dtype in ("f32", "f64"))
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, single thread, bounded sample.
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(args, a, seconds):
+    import oracle
+    oracle.build()
+    sample_n = min(len(a), 10_000_000)
+    sample = a[:sample_n]
+    times = []
+    t_end = time.perf_counter() + seconds
+    while True:
+        t0 = time.perf_counter()
+        oracle.sort(sample, args.dtype, True)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end or len(times) >= 10:
+            break
+    med = statistics.median(times)
+    return {
+        "value": sample_n / med / 1e9, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
+        "sample": f"first {sample_n:.0e} keys of the same array, sorted {len(times)} times "
+                  f"(median {med:.2f} s); scalar median-of-3 Quicksort, 1 thread",
+    }
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    a = make_input(args)
+    cb = cpu_baseline(args, a, max(3.0, args.cpu_seconds))
+    line = {
+        "impl": "reference", "metric": "sort throughput (GKeys/s)", "value": cb["value"],
+        "unit": "GKeys/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+        "data": "synthetic", "config": workload(args), "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": "GKeys/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm.
+# ---------------------------------------------------------------------------
+
+def to_device_bits(a, dtype, torch):
+    view = {2: np.int16, 4: np.int32, 8: np.int64, 16: np.int64}[inputs.KEY_BYTES[dtype]]
+    host = a if dtype in ("f32", "f64") else a.view(view)
+    return torch.from_numpy(np.ascontiguousarray(host)).cuda()
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2205_05982_gb300 as vq
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    vq.load()
+    kb = inputs.KEY_BYTES[args.dtype]
+
+    a = make_input(args)
+    src = to_device_bits(a, args.dtype, torch)
+    copies = [src.clone() for _ in range(args.steps + args.warmup)]
+    ws = vq.alloc_workspace(args.dtype, args.n)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        vq.sort_ws_(copies[i], ws, args.dtype)
+    torch.cuda.synchronize()
+    st = vq.stats(ws)
+    assert st["device_status"] == 0, st
+
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    vq.profile_reset()
+    vq.profile_enable(True)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        vq.sort_ws_(copies[args.warmup + i], ws, args.dtype)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    vq.profile_enable(False)
+    prof = vq.profile_read()
+    ms_total = e0.elapsed_time(e1)
+    st = vq.stats(ws)
+    assert st["device_status"] == 0, st
+    ms_tensor = torch.tensor([ms_total], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_tensor, op=dist.ReduceOp.MAX)
+    ms_total = float(ms_tensor.item())
+    ms_step = ms_total / args.steps
+
+    # spot check: the last timed output is sorted (codes non-decreasing)
+    out = copies[-1]
+    if args.dtype == "u64":
+        enc = out ^ torch.tensor(-2 ** 63, dtype=torch.int64, device=out.device)
+        assert bool((enc[1:] >= enc[:-1]).all())
+    del copies
+
+    # roofline of the dominant kernel (the persistent partition kernel)
+    part = prof.get("partition", {"ms": float("nan"), "launches": 1})
+    part_ms = part["ms"] / max(1, part["launches"])
+    part_bytes = 2 * kb * st["keys_partitioned"]
+    peak, peak_kind = hbm_peak()
+    achieved = part_bytes / (part_ms * 1e-3) / 1e9
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        key = f"{args.dtype}:{args.n}:{args.dist}"
+        if key in tr:
+            traffic = tr[key]["bytes_per_launch"]
+    except Exception:  # noqa: BLE001
+        pass
+    leaf_ms = sum(v["ms"] for k, v in prof.items() if k.startswith("leaf")) / args.steps
+    sort_bytes = part_bytes + 2 * kb * args.n
+    kernels = {k: {"ms_per_launch": v["ms"] / max(1, v["launches"]), "launches": v["launches"]}
+               for k, v in prof.items()}
+    gpu_launches = sum(v["launches"] for v in prof.values())
+
+    # end to end through the public host-buffer entry point (copies inside)
+    e2e_times = []
+    pinned = torch.empty(src.numel() * src.element_size(), dtype=torch.uint8, pin_memory=True)
+    host_view = pinned.numpy().view(a.dtype).reshape(a.shape)
+    for _ in range(args.e2e_steps + 1):
+        host_view[...] = a
+        t0 = time.perf_counter()
+        vq.sort_host(host_view, args.dtype)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_times = e2e_times[1:]
+    e2e_val = world * args.n * len(e2e_times) / sum(e2e_times) / 1e9
+
+    line = {
+        "metric": "sort throughput (GKeys/s), 1e8 keys per array",
+        "value": world * args.n / (ms_step * 1e-3) / 1e9,
+        "unit": "GKeys/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.dtype, "data": "synthetic",
+        "config": workload(args),
+        "roofline": {"bound": "hbm", "kernel": "k_partition (persistent partition levels)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": part_bytes},
+        "sort_roofline": {"bytes_per_step": sort_bytes,
+                          "achieved_gbs": sort_bytes / (ms_step * 1e-3) / 1e9,
+                          "frac": sort_bytes / (ms_step * 1e-3) / 1e9 / peak,
+                          "levels_run_keys": st["keys_partitioned"], "max_depth": st["max_depth"],
+                          "leaf_ms_per_step": leaf_ms},
+        "kernels": kernels,
+        "gpu_launches": gpu_launches,
+        "e2e": {"value": e2e_val, "unit": "GKeys/s", "h2d_bytes_per_step": args.n * kb,
+                "d2h_bytes_per_step": args.n * kb, "path": "vqsort_sort_host (pinned host buffer)"},
+        "clocks": clk,
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(args, a, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

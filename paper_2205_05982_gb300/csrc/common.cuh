@@ -226,8 +226,15 @@ __device__ __forceinline__ void bulk_load(void *smem_dst, const void *gsrc, uint
       : "memory");
 }
 // Orders this thread's generic-proxy accesses before later async-proxy (TMA)
-// accesses, for global and shared memory.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+// accesses: of shared memory (a buffer read by threads, then refilled by a
+// TMA copy) and of global memory (data written by other blocks, then read
+// by a TMA copy).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 
 // ---------------------------------------------------------------------------
 // Workspace layout (device memory, owned by the caller or by the library).
@@ -257,14 +264,14 @@ static_assert(sizeof(Header) % 64 == 0, "header size");
 struct SegDesc {
   unsigned long long begin, end;    // key indices [begin, end)
   unsigned long long piv_lo, piv_hi;// pivot code (piv_hi only for 16-byte keys)
-  unsigned int q0;                  // queue slot of tile 0 (= look-back status slot)
-  unsigned int ntiles;
+  unsigned long long cursor;        // write cursors (atomic): left keys written in bits
+                                    // 0..31, right keys written in bits 32..63
   unsigned int depth;               // partition levels above this range
   unsigned int flags;               // SEG_* bits
+  unsigned int ntiles;
   unsigned int tiles_done;          // tiles finished (atomic)
   unsigned int has_lt;              // some key < pivot was seen (atomic)
   unsigned int depth_limit;         // bound of its root range
-  unsigned int pad;
 };
 static_assert(sizeof(SegDesc) == 64, "segment descriptor size");
 
@@ -284,10 +291,6 @@ enum : unsigned int { LEAF_COPY = 8u };   // all keys equal: decode and copy onl
 
 // Work-queue item: bit 63 valid, bits 32..62 segment id, bits 0..31 tile.
 constexpr unsigned long long ITEM_VALID = 1ull << 63;
-// Look-back status word: bits 62..63 flag, bits 0..61 count of left keys.
-constexpr unsigned long long ST_AGG = 1ull << 62;
-constexpr unsigned long long ST_PFX = 2ull << 62;
-constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
 
 // Warp leaves handle ranges up to this many keys (32 lanes x 16 keys).
 constexpr unsigned WARP_LEAF_MAX = 512;
@@ -306,7 +309,6 @@ struct SortArgs {
   Header *hdr;
   SegDesc *segs;
   unsigned long long *items;
-  unsigned long long *status;
   LeafEntry *leaf_warp, *leaf_block, *fb;
   const unsigned long long *offsets;   // CSR offsets or null (one segment)
   unsigned long long n_total;

@@ -13,7 +13,8 @@ namespace vq {
 constexpr int PART_NT = 256;
 constexpr int PART_CPT = 8;
 constexpr int PART_WINDOW = PART_NT * PART_CPT * 16;   // bytes of one tile window
-constexpr int PART_SMEM = PART_WINDOW + 64;            // + staging slack
+constexpr int PART_SMEM = PART_WINDOW + 128;           // tile window (+ slack, 128-byte aligned)
+constexpr int PART_BLOCKS_PER_SM = 5;
 // Tile keys: the tile plus its 16-byte misalignment fits the window.
 __host__ __device__ constexpr unsigned part_tile_keys(int kb) { return (PART_WINDOW - 16) / kb; }
 

@@ -5,7 +5,7 @@
 //   - k_leaf_warp: one warp per range of <= 512 keys; each lane holds R keys
 //     (R = 1..16, the smallest that fits), padded with the all-ones code,
 //     which is the last value in sort order (Sec. 2.3 padding rule).
-//   - k_leaf_block: 1024 threads per range of up to the cutoff (16K keys);
+//   - k_leaf_block: cutoff/16 threads per range of up to the cutoff;
 //     cross-warp merge steps exchange registers through shared memory, and
 //     the sorted keys are staged in shared memory for coalesced stores.
 //     Ranges flagged all-equal are only decoded and copied.
@@ -70,11 +70,10 @@ template <int KB> __global__ void __launch_bounds__(256) k_leaf_warp(SortArgs a)
   }
 }
 
-template <int KB, int R>
+template <int KB, int R, int NT>
 __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, uint64_t b, unsigned len, bool raw,
                                            typename KT<KB>::Code *sx) {
   using C = typename KT<KB>::Code;
-  constexpr int NT = LEAF_NT;
   const unsigned t = threadIdx.x;
   C k[R];
 #pragma unroll
@@ -99,7 +98,9 @@ __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, u
   __syncthreads();
 }
 
-template <int KB> __global__ void __launch_bounds__(LEAF_NT, 1) k_leaf_block(SortArgs a) {
+// NT threads sort one range of up to 16*NT keys, R = P/NT keys per thread
+// where P is the range length rounded up to a power of two (>= NT).
+template <int KB, int NT> __global__ void __launch_bounds__(NT, NT <= 512 ? 2 : 1) k_leaf_block(SortArgs a) {
   using C = typename KT<KB>::Code;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_idx;
@@ -117,32 +118,33 @@ template <int KB> __global__ void __launch_bounds__(LEAF_NT, 1) k_leaf_block(Sor
     const bool raw = le.flags & SEG_RAW;
     const unsigned len = le.len;
     if (le.flags & LEAF_COPY) {
-      for (unsigned j = threadIdx.x; j < len; j += LEAF_NT) {
+      for (unsigned j = threadIdx.x; j < len; j += NT) {
         const C c = load_key<KB>(src, le.begin + j);
         store_key<KB>(a.keys, le.begin + j, decode<KB>(raw ? encode<KB>(c, a.codec) : c, a.codec));
       }
       continue;
     }
-    if (len <= 1024) block_leaf<KB, 1>(a, src, le.begin, len, raw, sx);
-    else if (len <= 2048) block_leaf<KB, 2>(a, src, le.begin, len, raw, sx);
-    else if (len <= 4096) block_leaf<KB, 4>(a, src, le.begin, len, raw, sx);
-    else if constexpr (KB <= 8) {
-      if (len <= 8192) block_leaf<KB, 8>(a, src, le.begin, len, raw, sx);
-      else block_leaf<KB, 16>(a, src, le.begin, len, raw, sx);
-    }
+    if (len <= NT) block_leaf<KB, 1, NT>(a, src, le.begin, len, raw, sx);
+    else if (len <= 2 * NT) block_leaf<KB, 2, NT>(a, src, le.begin, len, raw, sx);
+    else if (len <= 4 * NT) block_leaf<KB, 4, NT>(a, src, le.begin, len, raw, sx);
+    else if (len <= 8 * NT) block_leaf<KB, 8, NT>(a, src, le.begin, len, raw, sx);
+    else block_leaf<KB, 16, NT>(a, src, le.begin, len, raw, sx);
   }
 }
 
-template <int KB> int leaf_block_grid(size_t smem) {
+// Threads per block-leaf CTA for a cutoff: 16 keys per thread at the cutoff.
+constexpr int leaf_nt(unsigned cutoff) { return cutoff >= 16384 ? 1024 : cutoff >= 8192 ? 512 : 256; }
+
+template <int KB, int NT> int leaf_block_grid(size_t smem) {
   static int grid = 0;
   static size_t last = 0;
   if (!grid || last != smem) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_leaf_block<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_leaf_block<KB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)leaf_block_smem(KB, max_leaf_cutoff(KB)));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_leaf_block<KB>, LEAF_NT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_leaf_block<KB, NT>, NT, smem);
     grid = sms * (per > 0 ? per : 1);
     last = smem;
   }
@@ -162,8 +164,17 @@ template <int KB> int leaf_warp_grid() {
 }
 
 template <int KB> cudaError_t leaf_block_impl(const SortArgs &a, cudaStream_t s) {
-  const size_t smem = leaf_block_smem(KB, a.leaf_cutoff < 1024 ? 1024 : a.leaf_cutoff);
-  k_leaf_block<KB><<<leaf_block_grid<KB>(smem), LEAF_NT, smem, s>>>(a);
+  const unsigned C = a.leaf_cutoff < 1024 ? 1024 : a.leaf_cutoff;
+  const size_t smem = leaf_block_smem(KB, C);
+  if constexpr (KB == 16) {   // cutoff <= 4096: always 256 threads
+    k_leaf_block<KB, 256><<<leaf_block_grid<KB, 256>(smem), 256, smem, s>>>(a);
+  } else {
+    switch (leaf_nt(C)) {
+      case 1024: k_leaf_block<KB, 1024><<<leaf_block_grid<KB, 1024>(smem), 1024, smem, s>>>(a); break;
+      case 512: k_leaf_block<KB, 512><<<leaf_block_grid<KB, 512>(smem), 512, smem, s>>>(a); break;
+      default: k_leaf_block<KB, 256><<<leaf_block_grid<KB, 256>(smem), 256, smem, s>>>(a); break;
+    }
+  }
   return cudaGetLastError();
 }
 

@@ -51,10 +51,6 @@ __device__ __forceinline__ void sfc_seed(Sfc64 &s, uint64_t seed) {
 __device__ __forceinline__ uint32_t word(const uint4 &q, unsigned i) {
   return i == 0 ? q.x : i == 1 ? q.y : i == 2 ? q.z : q.w;
 }
-__device__ __forceinline__ void set_word(uint4 &q, unsigned i, uint32_t w) {
-  if (i == 0) q.x = w; else if (i == 1) q.y = w; else if (i == 2) q.z = w; else q.w = w;
-}
-
 template <int KB> __device__ __forceinline__ typename KT<KB>::Code key_at(const uint4 &q, unsigned v);
 template <> __device__ __forceinline__ uint32_t key_at<2>(const uint4 &q, unsigned v) {
   const uint32_t w = word(q, v >> 1);
@@ -68,20 +64,6 @@ template <> __device__ __forceinline__ U128 key_at<16>(const uint4 &q, unsigned)
   return U128{((uint64_t)q.y << 32) | q.x, ((uint64_t)q.w << 32) | q.z};
 }
 
-template <int KB> __device__ __forceinline__ void set_key(uint4 &q, unsigned v, typename KT<KB>::Code c);
-template <> __device__ __forceinline__ void set_key<2>(uint4 &q, unsigned v, uint32_t c) {
-  const uint32_t w = word(q, v >> 1);
-  set_word(q, v >> 1, (v & 1) ? ((w & 0xFFFFu) | (c << 16)) : ((w & 0xFFFF0000u) | (c & 0xFFFFu)));
-}
-template <> __device__ __forceinline__ void set_key<4>(uint4 &q, unsigned v, uint32_t c) { set_word(q, v, c); }
-template <> __device__ __forceinline__ void set_key<8>(uint4 &q, unsigned v, uint64_t c) {
-  set_word(q, 2 * v, (uint32_t)c);
-  set_word(q, 2 * v + 1, (uint32_t)(c >> 32));
-}
-template <> __device__ __forceinline__ void set_key<16>(uint4 &q, unsigned, U128 c) {
-  q = make_uint4((uint32_t)c.lo, (uint32_t)(c.lo >> 32), (uint32_t)c.hi, (uint32_t)(c.hi >> 32));
-}
-
 template <int KB> __device__ __forceinline__ typename KT<KB>::Code code_of(uint64_t lo, uint64_t hi) {
   if constexpr (KB == 16) return U128{lo, hi};
   else return (typename KT<KB>::Code)lo;
@@ -93,7 +75,7 @@ template <int KB> __device__ __forceinline__ void code_words(typename KT<KB>::Co
 
 // Shared scratch used by the range-level helpers (one per thread block).
 struct RangeScratch {
-  unsigned long long sid, q0, idx;
+  unsigned long long sid, q0, idx;   // q0: first queue slot of a new range
   int ok;
 };
 
@@ -164,14 +146,13 @@ __device__ void make_segment(const SortArgs &a, uint64_t b, uint64_t e, unsigned
       d.end = e;
       d.piv_lo = lo;
       d.piv_hi = hi;
-      d.q0 = (unsigned)q0;
-      d.ntiles = nt;
+      d.cursor = 0;
       d.depth = depth;
       d.flags = flags;
+      d.ntiles = nt;
       d.tiles_done = 0;
       d.has_lt = 0;
       d.depth_limit = depth_limit;
-      d.pad = 0;
     } else {
       raise_error(a, ERR_INTERNAL);
     }
@@ -181,10 +162,9 @@ __device__ void make_segment(const SortArgs &a, uint64_t b, uint64_t e, unsigned
   }
   __syncthreads();
   if (rs.ok) {
+    // the descriptor (written by thread 0, ordered by the barrier above) is
+    // published with each item's release store
     const unsigned long long q0 = rs.q0, sid = rs.sid;
-    for (unsigned k = threadIdx.x; k < nt; k += blockDim.x) st_relaxed(&a.status[q0 + k], 0);
-    __threadfence();
-    __syncthreads();
     for (unsigned k = threadIdx.x; k < nt; k += blockDim.x)
       st_release(&a.items[q0 + k], ITEM_VALID | (sid << 32) | k);
   }
@@ -277,7 +257,7 @@ __device__ void finish_range(const SortArgs &a, const SegDesc &sd, unsigned sid,
                              RangeScratch &rs) {
   using C = typename KT<KB>::Code;
   const uint64_t b = sd.begin, e = sd.end, m = e - b;
-  const uint64_t L = ld_relaxed(&a.status[sd.q0 + sd.ntiles - 1]) & ST_VAL;
+  const uint64_t L = ld_relaxed(&a.segs[sid].cursor) & 0xFFFFFFFFull;
   if (a.mode == MODE_PARTITION) {
     if (threadIdx.x == 0) {
       *a.out_left = L;
@@ -285,6 +265,7 @@ __device__ void finish_range(const SortArgs &a, const SegDesc &sd, unsigned sid,
     }
     return;
   }
+  if (a.test_stall && sid == 0) return;   // test hook: children never appear
   const unsigned parity = (sd.flags & SEG_PARITY) ^ 1u;   // keys now live in the other buffer
   const unsigned d1 = sd.depth + 1;
   if (threadIdx.x == 0) {
@@ -302,8 +283,7 @@ __device__ void finish_range(const SortArgs &a, const SegDesc &sd, unsigned sid,
   } else if (L == m) {
     // Degenerate partition (Algorithm 1): every key <= pivot.
     if (threadIdx.x == 0) atomicAdd(&a.hdr->degenerate, 1ull);
-    const unsigned has_lt = ld_relaxed32(&a.segs[sid].has_lt);
-    if (!has_lt) {
+    if (!ld_relaxed32(&a.segs[sid].has_lt)) {
       emit_equal(a, b, m, parity, rs);   // min == max: already sorted
       handed += m;
     } else if (d1 >= sd.depth_limit) {
@@ -328,10 +308,9 @@ __device__ void finish_range(const SortArgs &a, const SegDesc &sd, unsigned sid,
 // Work claiming and look-back.
 // ---------------------------------------------------------------------------
 
-// Thread 0: claims the next ticket and waits (bounded) for its item. Returns
-// 0 when all keys are placed, on abort, or on a timeout.
-__device__ int claim(const SortArgs &a, unsigned long long &item) {
-  const unsigned long long t = atomicAdd(&a.hdr->head, 1ull);
+// Thread 0: waits (bounded) for the item of an already claimed ticket.
+// Returns 0 when all keys are placed, on abort, or on a timeout.
+__device__ int wait_ticket(const SortArgs &a, unsigned long long t, unsigned long long &item) {
   for (unsigned it = 0;; ++it) {
     if (t < a.cap_q) {
       const unsigned long long v = ld_acquire(&a.items[t]);
@@ -350,68 +329,87 @@ __device__ int claim(const SortArgs &a, unsigned long long &item) {
   }
 }
 
-// Warp 0: publishes the tile's left count and returns the left keys of all
-// earlier tiles of the range (decoupled look-back over a 32-tile window).
-// Returns ~0 if the wait gave up.
-__device__ uint64_t lookback(const SortArgs &a, unsigned long long *st, unsigned i, uint64_t tileL,
-                             bool stall) {
-  const unsigned lane = threadIdx.x & 31;
-  if (i == 0) {
-    if (lane == 0 && !stall) st_relaxed(&st[0], ST_PFX | tileL);
-    return 0;
-  }
-  if (lane == 0) st_relaxed(&st[i], ST_AGG | tileL);
-  uint64_t excl = 0;
-  long long j = (long long)i - 1;
-  for (;;) {
-    const long long idx = j - (long long)lane;
-    uint64_t v = ST_PFX;   // before tile 0: an empty inclusive prefix
-    for (unsigned it = 0;; ++it) {
-      if (idx >= 0) v = ld_relaxed(&st[idx]);
-      if (__all_sync(FULL, (v >> 62) != 0)) break;
-      const int give_up = it >= a.spin_limit || aborted(a);
-      if (__any_sync(FULL, give_up)) {
-        if (lane == 0 && it >= a.spin_limit) raise_error(a, ERR_TIMEOUT);
-        return ~0ull;
-      }
-      if (it > 8) __nanosleep(64);
-    }
-    const unsigned pm = __ballot_sync(FULL, (v >> 62) == 2);
-    const unsigned first = pm ? (unsigned)(__ffs(pm) - 1) : 31u;
-    uint64_t val = lane <= first ? (v & ST_VAL) : 0;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) val += __shfl_xor_sync(FULL, val, o);
-    excl += val;
-    if (pm) break;
-    j -= 32;
-  }
-  if (lane == 0) st_relaxed(&st[i], ST_PFX | (excl + tileL));
-  return excl;
+// Thread 0: claims the next ticket and waits for its item.
+__device__ int claim(const SortArgs &a, unsigned long long &item) {
+  return wait_ticket(a, atomicAdd(&a.hdr->head, 1ull), item);
 }
 
-// Writes `len` keys from shared memory (key index s, placed so that its byte
-// offset matches `gdst` modulo 16) to global memory: 16-byte stores for the
-// aligned body, single keys for the ragged ends.
-template <int KB>
-__device__ __forceinline__ void store_run(void *gdst, const unsigned char *smem, unsigned s, unsigned len) {
-  using M = typename KT<KB>::Mem;
-  constexpr unsigned V = 16 / KB;
-  const uintptr_t ga = (uintptr_t)gdst;
-  const unsigned head = min(len, (unsigned)(((16 - (ga & 15)) & 15) / KB));
-  const unsigned body = (len - head) / V;
-  const unsigned tail = len - head - body * V;
-  const M *sm = (const M *)smem + s;
-  M *g = (M *)gdst;
-  if (threadIdx.x < head) g[threadIdx.x] = sm[threadIdx.x];
-  const uint4 *sb = (const uint4 *)(sm + head);
-  uint4 *gb = (uint4 *)(g + head);
-  for (unsigned c = threadIdx.x; c < body; c += NT) gb[c] = sb[c];
-  if (threadIdx.x < tail) g[head + body * V + threadIdx.x] = sm[head + body * V + threadIdx.x];
+// Thread 0: is the item of ticket t already published?
+__device__ __forceinline__ bool probe_ticket(const SortArgs &a, unsigned long long t, unsigned long long &item) {
+  if (t >= a.cap_q) return false;
+  const unsigned long long v = ld_acquire(&a.items[t]);
+  if (v & ITEM_VALID) {
+    item = v;
+    return true;
+  }
+  return false;
 }
 
 template <int KB> __device__ __forceinline__ typename KT<KB>::Mem to_mem(typename KT<KB>::Code c) {
   if constexpr (KB == 16) return c;
   else return (typename KT<KB>::Mem)c;
+}
+
+// Pass 1 over the tile window: left keys (code <= pivot), valid keys, and
+// whether some key is < pivot. Chunks fully inside the tile skip the
+// per-key bounds test.
+template <int KB, bool RAW>
+__device__ __forceinline__ void count_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
+                                           unsigned hi, typename KT<KB>::Code piv, unsigned &nL,
+                                           unsigned &nV, int &anyLt) {
+  using C = typename KT<KB>::Code;
+  constexpr unsigned V = 16 / KB;
+#pragma unroll 2
+  for (int j = 0; j < PART_CPT; ++j) {
+    const unsigned c = threadIdx.x + j * NT;
+    const uint4 q = c < nwc ? sw[c] : make_uint4(0, 0, 0, 0);
+    const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
+#pragma unroll
+    for (unsigned v = 0; v < V; ++v) {
+      const unsigned off = 16 * c + v * KB;
+      const bool valid = full || (off >= lo && off < hi);
+      C k = key_at<KB>(q, v);
+      if (RAW) k = encode<KB>(k, a.codec);
+      nL += (valid && !lt(piv, k));
+      nV += valid;
+      anyLt |= (valid && lt(k, piv));
+    }
+  }
+}
+
+// Pass 2 over the tile window: every valid key goes to its ballot rank in
+// the left run (outL) or the right run (outR).
+template <int KB, bool RAW, bool DEC>
+__device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
+                                             unsigned hi, typename KT<KB>::Code piv,
+                                             typename KT<KB>::Mem *outL, typename KT<KB>::Mem *outR,
+                                             unsigned runL, unsigned runR) {
+  using C = typename KT<KB>::Code;
+  constexpr unsigned V = 16 / KB;
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned ltm = (1u << lane) - 1u;
+#pragma unroll 2
+  for (int j = 0; j < PART_CPT; ++j) {
+    const unsigned c = threadIdx.x + j * NT;
+    const uint4 q = c < nwc ? sw[c] : make_uint4(0, 0, 0, 0);
+    const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
+#pragma unroll
+    for (unsigned v = 0; v < V; ++v) {
+      const unsigned off = 16 * c + v * KB;
+      const bool valid = full || (off >= lo && off < hi);
+      C k = key_at<KB>(q, v);
+      if (RAW) k = encode<KB>(k, a.codec);
+      const bool le = !lt(piv, k);
+      const unsigned bl = __ballot_sync(FULL, valid && le), br = __ballot_sync(FULL, valid && !le);
+      if (valid) {
+        const typename KT<KB>::Mem out = to_mem<KB>(DEC ? decode<KB>(k, a.codec) : k);
+        if (le) outL[runL + __popc(bl & ltm)] = out;
+        else outR[runR + __popc(br & ltm)] = out;
+      }
+      runL += __popc(bl);
+      runR += __popc(br);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -467,11 +465,49 @@ template <int KB> __global__ void __launch_bounds__(NT) k_seed(SortArgs a) {
   }
 }
 
-// The persistent partition kernel.
-template <int KB> __global__ void __launch_bounds__(NT, 3) k_partition(SortArgs a) {
+// Loads the descriptor of `item`'s range (through L2) into `seg`.
+__device__ __forceinline__ void load_desc(const SortArgs &a, unsigned long long item, SegDesc &seg) {
+  const unsigned sid = (unsigned)((item >> 32) & 0x7FFFFFFFu);
+  const unsigned long long *d = (const unsigned long long *)&a.segs[sid];
+  unsigned long long w[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) w[k] = __ldcg(d + k);
+  unsigned long long *sw = (unsigned long long *)&seg;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sw[k] = w[k];
+}
+
+// Starts the TMA bulk copy of the tile's 16-byte-aligned window into `buf`.
+// The window may include up to 15 bytes on each side that belong to
+// neighbouring ranges; they are never used (and never cross a page).
+template <int KB>
+__device__ __forceinline__ void issue_tile(const SortArgs &a, unsigned long long item, const SegDesc &seg,
+                                           unsigned char *buf, uint64_t *bar) {
+  constexpr unsigned T = part_tile_keys(KB);
+  const unsigned i = (unsigned)(item & 0xFFFFFFFFu);
+  const uint64_t b = seg.begin, e = seg.end;
+  const bool par = seg.flags & SEG_PARITY;
+  const unsigned char *src = (const unsigned char *)(par ? a.alt : a.keys);
+  const uint64_t t0 = b + (uint64_t)i * T;
+  const unsigned cnt = (unsigned)min((uint64_t)T, e - t0);
+  const uintptr_t g0 = (uintptr_t)(src + t0 * KB), g1 = g0 + (uintptr_t)cnt * KB;
+  const uintptr_t w0 = g0 & ~(uintptr_t)15, w1 = (g1 + 15) & ~(uintptr_t)15;
+  fence_proxy_async_global();
+  mbar_arrive_expect_tx(bar, (uint32_t)(w1 - w0));
+  bulk_load(buf, (const void *)w0, (uint32_t)(w1 - w0), bar);
+}
+
+// The persistent partition kernel. Per tile: one TMA copy into the shared
+// window, a counting pass, one atomic on the range's write cursors that
+// reserves this tile's slots on both sides (the GPU form of the bidirectional
+// write positions of Sec. 2.1: the order of keys within a side is free, so
+// tiles need not wait for one another), and a scatter pass that writes every
+// key straight from its ballot rank to global memory (each warp store is two
+// contiguous runs). A block needs only the window and few registers, so
+// several blocks per SM keep enough bytes in flight.
+template <int KB> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER_SM) k_partition(SortArgs a) {
   using C = typename KT<KB>::Code;
   using M = typename KT<KB>::Mem;
-  constexpr unsigned V = 16 / KB;
   constexpr unsigned T = part_tile_keys(KB);
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t s_bar;
@@ -479,12 +515,15 @@ template <int KB> __global__ void __launch_bounds__(NT, 3) k_partition(SortArgs 
   __shared__ unsigned long long s_item;
   __shared__ int s_go, s_fin;
   __shared__ unsigned s_wL[NWARP], s_wV[NWARP], s_bL[NWARP], s_bR[NWARP];
-  __shared__ unsigned long long s_pfx, s_dstR;
-  __shared__ unsigned s_tileL, s_tileR, s_sL, s_sR;
+  __shared__ unsigned long long s_cur;
   __shared__ RangeScratch rs;
+  __shared__ __align__(16) unsigned char s_sample[SAMPLE * sizeof(C) + 64 * 8];
 
   const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) mbar_init(&s_bar, 1);
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
   uint32_t phase = 0;
 
@@ -495,50 +534,12 @@ template <int KB> __global__ void __launch_bounds__(NT, 3) k_partition(SortArgs 
       s_go = go;
       if (go) {
         s_item = item;
-        const unsigned sid = (unsigned)((item >> 32) & 0x7FFFFFFFu);
-        const unsigned long long *src = (const unsigned long long *)&a.segs[sid];
-        unsigned long long *dstw = (unsigned long long *)&s_seg;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) dstw[w] = __ldcg(src + w);
+        load_desc(a, item, s_seg);
+        issue_tile<KB>(a, item, s_seg, smem, &s_bar);
       }
     }
     __syncthreads();
     if (!s_go) break;
-
-    const unsigned sid = (unsigned)((s_item >> 32) & 0x7FFFFFFFu);
-    const unsigned i = (unsigned)(s_item & 0xFFFFFFFFu);
-    const uint64_t b = s_seg.begin, e = s_seg.end;
-    const bool par = s_seg.flags & SEG_PARITY, raw = s_seg.flags & SEG_RAW;
-    const C piv = code_of<KB>(s_seg.piv_lo, s_seg.piv_hi);
-    const unsigned char *src = (const unsigned char *)(par ? a.alt : a.keys);
-    unsigned char *dst = (unsigned char *)(par ? a.keys : a.alt);
-    const uint64_t t0 = b + (uint64_t)i * T;
-    const unsigned cnt = (unsigned)min((uint64_t)T, e - t0);
-    const uintptr_t g0 = (uintptr_t)(src + t0 * KB), g1 = g0 + (uintptr_t)cnt * KB;
-    const uintptr_t w0 = g0 & ~(uintptr_t)15;
-    const uintptr_t a0 = (g0 + 15) & ~(uintptr_t)15, a1 = g1 & ~(uintptr_t)15;
-    const bool body = a0 < a1;
-
-    // ---- load the tile: TMA bulk copy of the aligned body, plain loads of the ragged ends
-    if (tid == 0) {
-      fence_proxy_async();
-      if (body) {
-        mbar_arrive_expect_tx(&s_bar, (uint32_t)(a1 - a0));
-        bulk_load(smem + (a0 - w0), (const void *)a0, (uint32_t)(a1 - a0), &s_bar);
-      } else {
-        mbar_arrive_expect_tx(&s_bar, 0);
-      }
-    }
-    if constexpr (KB < 16) {
-      const uintptr_t hend = body ? a0 : g1;
-      const unsigned nh = (unsigned)((hend - g0) / KB);
-      const unsigned ntl = body ? (unsigned)((g1 - a1) / KB) : 0u;
-      if (tid < nh) {
-        *(M *)(smem + (g0 - w0) + tid * KB) = __ldcg((const M *)g0 + tid);
-      } else if (tid >= 64 && tid < 64 + ntl) {
-        *(M *)(smem + (a1 - w0) + (tid - 64) * KB) = __ldcg((const M *)a1 + (tid - 64));
-      }
-    }
     {
       unsigned it = 0;
       while (!mbar_try_wait(&s_bar, phase)) {
@@ -547,41 +548,30 @@ template <int KB> __global__ void __launch_bounds__(NT, 3) k_partition(SortArgs 
           break;
         }
       }
+      phase ^= 1;
     }
-    phase ^= 1;
-    __syncthreads();
 
-    // ---- tile chunks into registers (raw root tiles are encoded here)
+    const SegDesc &sg = s_seg;
+    const unsigned sid = (unsigned)((s_item >> 32) & 0x7FFFFFFFu);
+    const unsigned i = (unsigned)(s_item & 0xFFFFFFFFu);
+    const uint64_t b = sg.begin, e = sg.end;
+    const bool par = sg.flags & SEG_PARITY, raw = sg.flags & SEG_RAW;
+    const C piv = code_of<KB>(sg.piv_lo, sg.piv_hi);
+    const unsigned char *src = (const unsigned char *)(par ? a.alt : a.keys);
+    M *dst = (M *)(par ? a.keys : a.alt);
+    const uint64_t t0 = b + (uint64_t)i * T;
+    const unsigned cnt = (unsigned)min((uint64_t)T, e - t0);
+    const uintptr_t g0 = (uintptr_t)(src + t0 * KB), g1 = g0 + (uintptr_t)cnt * KB;
+    const uintptr_t w0 = g0 & ~(uintptr_t)15;
     const unsigned nwc = (unsigned)((((g1 + 15) & ~(uintptr_t)15) - w0) / 16);
     const unsigned lo = (unsigned)(g0 - w0), hi = (unsigned)(g1 - w0);
-    uint4 ch[PART_CPT];
     const uint4 *sw = (const uint4 *)smem;
-#pragma unroll
-    for (int j = 0; j < PART_CPT; ++j) {
-      const unsigned c = tid + j * NT;
-      ch[j] = c < nwc ? sw[c] : make_uint4(0, 0, 0, 0);
-      if (raw) {
-#pragma unroll
-        for (unsigned v = 0; v < V; ++v) set_key<KB>(ch[j], v, encode<KB>(key_at<KB>(ch[j], v), a.codec));
-      }
-    }
 
     // ---- pass 1: per-warp counts of left and valid keys
     unsigned nL = 0, nV = 0;
     int anyLt = 0;
-#pragma unroll
-    for (int j = 0; j < PART_CPT; ++j) {
-#pragma unroll
-      for (unsigned v = 0; v < V; ++v) {
-        const unsigned off = 16 * (tid + j * NT) + v * KB;
-        const bool valid = off >= lo && off < hi;
-        const C c = key_at<KB>(ch[j], v);
-        const bool le = !lt(piv, c);
-        nL += (valid && le);
-        nV += valid;
-        anyLt |= (valid && lt(c, piv));
-      }
-    }
+    if (raw) count_tile<KB, true>(a, sw, nwc, lo, hi, piv, nL, nV, anyLt);
+    else count_tile<KB, false>(a, sw, nwc, lo, hi, piv, nL, nV, anyLt);
     nL = __reduce_add_sync(FULL, nL);
     nV = __reduce_add_sync(FULL, nV);
     if (lane == 0) {
@@ -590,7 +580,7 @@ template <int KB> __global__ void __launch_bounds__(NT, 3) k_partition(SortArgs 
     }
     anyLt = __syncthreads_or(anyLt);
 
-    // ---- block scan of warp counts, then look-back across tiles
+    // ---- block scan of warp counts, then reserve this tile's output slots
     if (warp == 0) {
       unsigned xL = lane < NWARP ? s_wL[lane] : 0, xV = lane < NWARP ? s_wV[lane] : 0;
       unsigned iL = xL, iV = xV;
@@ -599,79 +589,45 @@ template <int KB> __global__ void __launch_bounds__(NT, 3) k_partition(SortArgs 
         const unsigned yL = __shfl_up_sync(FULL, iL, o), yV = __shfl_up_sync(FULL, iV, o);
         if (lane >= (unsigned)o) { iL += yL; iV += yV; }
       }
-      const unsigned totL = __shfl_sync(FULL, iL, NWARP - 1), totV = __shfl_sync(FULL, iV, NWARP - 1);
       if (lane < NWARP) {
         s_bL[lane] = iL - xL;
         s_bR[lane] = (iV - xV) - (iL - xL);
       }
-      const bool stall = a.test_stall && sid == 0;
-      const uint64_t excl = lookback(a, a.status + s_seg.q0, i, totL, stall);
-      if (lane == 0) {
-        s_pfx = excl;
-        s_tileL = totL;
-        s_tileR = totV - totL;
-        if (excl != ~0ull) {
-          const uint64_t rightPrefix = (uint64_t)i * T - excl;
-          const uint64_t dstR = e - rightPrefix - (totV - totL);
-          const uintptr_t gL = (uintptr_t)(dst + (b + excl) * KB), gR = (uintptr_t)(dst + dstR * KB);
-          const unsigned sL = (unsigned)((gL & 15) / KB);
-          s_sL = sL;
-          s_sR = ((sL + totL + V - 1) / V) * V + (unsigned)((gR & 15) / KB);
-          s_dstR = dstR;
-        }
+      if (lane == NWARP - 1) {
+        const unsigned long long add = ((unsigned long long)(iV - iL) << 32) | iL;
+        s_cur = atomicAdd(&a.segs[sid].cursor, add);
+        if (anyLt) atomicOr(&a.segs[sid].has_lt, 1u);
       }
     }
     __syncthreads();
-    if (s_pfx == ~0ull) break;
 
-    // ---- pass 2: ballot compaction into the staging buffer (reuses the window)
+    // ---- pass 2: ballot ranks -> direct global stores. Left keys fill the
+    // range from its start, right keys from its end.
     {
-      unsigned runL = s_bL[warp], runR = s_bR[warp];
-      const unsigned sL = s_sL, sR = s_sR;
-      const unsigned ltm = (1u << lane) - 1u;
-      M *stage = (M *)smem;
-      const bool dec = a.mode == MODE_PARTITION;
-#pragma unroll
-      for (int j = 0; j < PART_CPT; ++j) {
-#pragma unroll
-        for (unsigned v = 0; v < V; ++v) {
-          const unsigned off = 16 * (tid + j * NT) + v * KB;
-          const bool valid = off >= lo && off < hi;
-          const C c = key_at<KB>(ch[j], v);
-          const bool le = !lt(piv, c);
-          const unsigned bl = __ballot_sync(FULL, valid && le), br = __ballot_sync(FULL, valid && !le);
-          if (valid) {
-            const unsigned pos = le ? sL + runL + __popc(bl & ltm) : sR + runR + __popc(br & ltm);
-            stage[pos] = to_mem<KB>(dec ? decode<KB>(c, a.codec) : c);
-          }
-          runL += __popc(bl);
-          runR += __popc(br);
-        }
-      }
+      const unsigned long long cur = s_cur;
+      const unsigned tileL = s_bL[NWARP - 1] + s_wL[NWARP - 1];
+      const unsigned tileR = cnt - tileL;
+      M *outL = dst + b + (cur & 0xFFFFFFFFull);
+      M *outR = dst + (e - (cur >> 32) - tileR);
+      const unsigned runL = s_bL[warp], runR = s_bR[warp];
+      if (a.mode == MODE_PARTITION) scatter_tile<KB, true, true>(a, sw, nwc, lo, hi, piv, outL, outR, runL, runR);
+      else if (raw) scatter_tile<KB, true, false>(a, sw, nwc, lo, hi, piv, outL, outR, runL, runR);
+      else scatter_tile<KB, false, false>(a, sw, nwc, lo, hi, piv, outL, outR, runL, runR);
     }
+    fence_proxy_async_smem();   // the next TMA copy reuses the window
     __syncthreads();
 
-    // ---- write both runs with 16-byte stores
-    store_run<KB>(dst + (b + s_pfx) * KB, smem, s_sL, s_tileL);
-    store_run<KB>(dst + s_dstR * KB, smem, s_sR, s_tileR);
-    fence_proxy_async();   // the next TMA copy reuses the window
-
-    // ---- range completion
-    if (anyLt && tid == 0) atomicOr(&a.segs[sid].has_lt, 1u);
-    __threadfence();
-    __syncthreads();
+    // ---- range completion: one release/acquire by thread 0 covers the
+    // whole block's stores (ordered before it by the barrier)
     if (tid == 0) {
+      __threadfence();
       const unsigned prev = atomicAdd(&a.segs[sid].tiles_done, 1u);
-      const int fin = prev == s_seg.ntiles - 1;
+      const int fin = prev == sg.ntiles - 1;
       if (fin) __threadfence();
       s_fin = fin;
     }
     __syncthreads();
-    if (s_fin) {
-      __threadfence();
-      finish_range<KB>(a, s_seg, sid, smem, rs);
-    }
-    __syncthreads();
+    if (s_fin) finish_range<KB>(a, sg, sid, s_sample, rs);
   }
 }
 

@@ -24,8 +24,16 @@ template <class C, int R> __device__ __forceinline__ void column_sort(C (&k)[R])
 #undef VQ_CE
 }
 
+// One side of a compare-exchange whose partner lives in another thread: the
+// lower position keeps the minimum, the upper one the maximum. Equal codes
+// are identical bit patterns, so either choice is right on ties.
+__device__ __forceinline__ uint32_t keep(uint32_t mine, uint32_t other, bool lower) {
+  const uint32_t mn = umin(mine, other), mx = umax(mine, other);
+  return lower ? mn : mx;
+}
 template <class C> __device__ __forceinline__ C keep(const C &mine, const C &other, bool lower) {
-  return lower ? cmin(mine, other) : cmax(mine, other);
+  const bool take = lt(other, mine) != !lower;
+  return take ? other : mine;
 }
 
 // One merge step. `t` is the thread's index in the sorting group; steps whose

@@ -64,7 +64,7 @@ unsigned leaf_cutoff_for(int kb) {
 // Workspace layout.
 // ---------------------------------------------------------------------------
 struct Layout {
-  size_t hdr, segs, items, status, lw, lb, fb, alt, total;
+  size_t hdr, segs, items, lw, lb, fb, alt, total;
   unsigned cap_q, cap_segs, cap_lw, cap_lb, cap_fb;
 };
 
@@ -92,7 +92,6 @@ Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_lim
   L.hdr = off; off = align256(off + sizeof(Header));
   L.segs = off; off = align256(off + cap_segs * sizeof(SegDesc));
   L.items = off; off = align256(off + cap_q * 8);
-  L.status = off; off = align256(off + cap_q * 8);
   L.lw = off; off = align256(off + cap_lw * sizeof(LeafEntry));
   L.lb = off; off = align256(off + cap_lb * sizeof(LeafEntry));
   L.fb = off; off = align256(off + cap_fb * sizeof(LeafEntry));
@@ -248,7 +247,6 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   a.hdr = (Header *)(w + L.hdr);
   a.segs = (SegDesc *)(w + L.segs);
   a.items = (unsigned long long *)(w + L.items);
-  a.status = (unsigned long long *)(w + L.status);
   a.leaf_warp = (LeafEntry *)(w + L.lw);
   a.leaf_block = (LeafEntry *)(w + L.lb);
   a.fb = (LeafEntry *)(w + L.fb);
