@@ -132,6 +132,28 @@ vq_status vqsort_partition(vq_dtype dt, const void *d_in, void *d_out, size_t n,
 vq_status vqsort_choose_pivot(vq_dtype dt, const void *d_keys, size_t n, uint64_t seed,
                               int ascending, void *d_pivot_out, void *stream);
 
+/* One Partition, as vqsort_partition, that allocates nothing. The paper has
+   no counterpart: this entry point exists for callers that must not call
+   cudaMalloc while they work, because cudaMalloc can synchronize the device
+   and can fail once a fixed memory budget is used up (a latency-bound
+   serving loop, code running inside another allocator's hooks).
+   Its scratch (counters, the range descriptor and the tile queue) is a
+   fixed array of about 513 KiB in device memory that belongs to the loaded
+   library: every GPU that loads libvqsort.so holds it until the process
+   exits. Limit: n <= 65536 * ((32768 - 16) / key bytes) keys (about 1.07e9
+   2-byte, 5.4e8 4-byte, 2.7e8 8-byte, 1.3e8 16-byte keys); larger n returns
+   VQ_ERR_INVALID before anything is launched.
+   The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress) with that device current; make that first call
+   before any stream capture. Every call clears the counters and queue it
+   needs, so a call never depends on the previous one, but all calls share
+   the one array: calls that overlap on the GPU (different streams, or
+   different host threads) race and give wrong results. Device-side
+   timeouts are not reported by this entry point. */
+vq_status vqsort_partition_noalloc(vq_dtype dt, const void *d_in, void *d_out, size_t n,
+                                   const void *h_pivot, int ascending, uint64_t *d_left_count,
+                                   void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Status, statistics, options, profiling.                                 */
 /* ---------------------------------------------------------------------- */
