@@ -33,6 +33,19 @@ from paper_2205_05982_gb300 import inputs  # noqa: E402
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+# sources of the partition kernel: a recorded DRAM traffic figure is used
+# only while these files are unchanged since the capture
+KERNEL_SOURCES = ("paper_2205_05982_gb300/csrc/partition.cu", "paper_2205_05982_gb300/csrc/common.cuh",
+                  "paper_2205_05982_gb300/csrc/launch.h")
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -46,6 +59,11 @@ def parse():
     p.add_argument("--dist", default="uniform")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the per-dtype, batched and served measurements")
+    p.add_argument("--served-requests", type=int, default=10_000)
     return p.parse_args()
 
 
@@ -182,10 +200,142 @@ class Clocks:
 # GPU arm.
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(value: float, dist=None) -> float:
+    """The slowest rank's time: every rank gets the maximum (any backend)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def to_device_bits(a, dtype, torch):
     view = {2: np.int16, 4: np.int32, 8: np.int64, 16: np.int64}[inputs.KEY_BYTES[dtype]]
     host = a if dtype in ("f32", "f64") else a.view(view)
     return torch.from_numpy(np.ascontiguousarray(host)).cuda()
+
+
+def time_sorts(vq, torch, copies, ws, dtype, warmup):
+    """Sorts copies[0:warmup] untimed, then each remaining copy; returns
+    (ms per sort, stats of the last sort, per-kernel profile)."""
+    for i in range(warmup):
+        vq.sort_ws_(copies[i], ws, dtype)
+    torch.cuda.synchronize()
+    vq.profile_reset()
+    vq.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for c in copies[warmup:]:
+        vq.sort_ws_(c, ws, dtype)
+    e1.record()
+    torch.cuda.synchronize()
+    vq.profile_enable(False)
+    prof = vq.profile_read()
+    st = vq.stats(ws)
+    return e0.elapsed_time(e1) / (len(copies) - warmup), st, prof
+
+
+def extra_dtypes(vq, torch, peak, n):
+    """The other key types of the 1e8-keys-per-dtype workload (uniform)."""
+    out = {}
+    for dt in ("f32", "i32", "i16"):
+        a = inputs.make(dt, n, "uniform", specials=dt == "f32")
+        src = to_device_bits(a, dt, torch)
+        copies = [src.clone() for _ in range(4)]
+        ws = vq.alloc_workspace(dt, n)
+        ms, st, prof = time_sorts(vq, torch, copies, ws, dt, 1)
+        kb = inputs.KEY_BYTES[dt]
+        part = prof.get("partition", {"ms": float("nan"), "launches": 1})
+        part_ms = part["ms"] / max(1, part["launches"])
+        pb = 2 * kb * st["keys_partitioned"]
+        out[dt] = {"gkeys_per_s": n / (ms * 1e-3) / 1e9, "ms": ms,
+                   "partition_frac": pb / (part_ms * 1e-3) / 1e9 / peak,
+                   "sort_frac": (pb + 2 * kb * n) / (ms * 1e-3) / 1e9 / peak,
+                   "max_depth": st["max_depth"]}
+        del copies, src, ws
+        torch.cuda.empty_cache()
+    return out
+
+
+def extra_batched(vq, torch, reps=5):
+    """16,384 arrays, sizes log-uniform in [16, 65536], uniform u32 keys:
+    one autotuned segmented sort replayed as a CUDA graph vs one plain sort
+    launch set per array. Outputs are compared byte for byte."""
+    from paper_2205_05982_gb300 import batch
+    res = {}
+    for dt in ("u32", "f32"):
+        sizes = inputs.segment_sizes(16384, 16, 65536)
+        off = inputs.offsets_from_sizes(sizes)
+        n = int(off[-1])
+        a = inputs.make(dt, n, "uniform", seed=7, specials=dt == "f32")
+        src = to_device_bits(a, dt, torch)
+        tune = batch.autotune(src.clone(), off, dt, reps=2)
+        b = batch.SegmentedBatch(src.clone(), off, dt, settings=tune["settings"])
+        b.capture()
+        g_ms = []
+        for _ in range(reps):
+            b.keys.copy_(src)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(b.stream)
+            with torch.cuda.stream(b.stream):
+                b.graph.replay()
+            e1.record(b.stream)
+            torch.cuda.synchronize()
+            g_ms.append(e0.elapsed_time(e1))
+        graph_out = b.keys.clone()
+        each = src.clone()
+        ws1 = vq.alloc_workspace(dt, int(sizes.max()), 1)
+        p_ms = []
+        for _ in range(max(1, reps // 2)):
+            each.copy_(src)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            batch.sort_each(each, off, dt, ws=ws1)
+            e1.record()
+            torch.cuda.synchronize()
+            p_ms.append(e0.elapsed_time(e1))
+        same = bool(torch.equal(graph_out, each))
+        gm, pm = float(np.median(g_ms)), float(np.median(p_ms))
+        res[dt] = {"arrays": int(sizes.size), "keys": n, "graph_ms": gm, "per_array_ms": pm,
+                   "graph_gkeys_per_s": n / (gm * 1e-3) / 1e9,
+                   "per_array_gkeys_per_s": n / (pm * 1e-3) / 1e9, "speedup": pm / gm,
+                   "identical_output": same, "tuned": tune["settings"],
+                   "tuned_ms": tune["ms"], "default_ms": tune["default_ms"]}
+        del b, src, each
+        torch.cuda.empty_cache()
+    return res
+
+
+def extra_served(vq, torch, num):
+    """Poisson stream of `num` requests, sizes log-uniform in [1e3, 1e7],
+    key type uniform over {i16, u32, f32, u64, kv64}, admitted under a 40 GB
+    budget: saturated capacity, then arrivals at 0.8 x capacity served with
+    continuous batching (8 slots) and one at a time (plain)."""
+    from paper_2205_05982_gb300 import serve
+    hi = 10_000_000
+    sources = {}
+    for dt in ("i16", "u32", "f32", "u64"):
+        sources[dt] = to_device_bits(inputs.make(dt, hi, "uniform", seed=3, specials=dt == "f32"), dt, torch)
+    sources["kv64"] = to_device_bits(inputs.kv_pairs(hi, seed=3), "kv64", torch)
+    server = serve.Server(slots=8, budget_bytes=40 * 10**9, max_keys=hi)
+    burst = serve.poisson_requests(num, 1e12, sources, seed=5)      # all arrive at once
+    sat = server.run(burst)
+    rate = 0.8 * sat["requests"] / (sat["span_ms"] * 1e-3)
+    reqs = serve.poisson_requests(num, rate, sources, seed=6)
+    served = server.run(reqs)
+    plain = serve.run_plain(serve.poisson_requests(num, rate, sources, seed=6), max_keys=hi)
+    del server, sources
+    torch.cuda.empty_cache()
+    return {"requests": num, "rate_per_s": rate, "saturated": sat, "served": served, "plain": plain,
+            "p99_speedup": plain["p99_ms"] / served["p99_ms"],
+            "throughput_ratio": served["gkeys_per_s"] / plain["gkeys_per_s"]}
 
 
 def run_gpu(args):
@@ -236,10 +386,7 @@ def run_gpu(args):
     ms_total = e0.elapsed_time(e1)
     st = vq.stats(ws)
     assert st["device_status"] == 0, st
-    ms_tensor = torch.tensor([ms_total], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_tensor, op=dist.ReduceOp.MAX)
-    ms_total = float(ms_tensor.item())
+    ms_total = max_over_ranks(ms_total, dist if world > 1 else None)
     ms_step = ms_total / args.steps
 
     # spot check: the last timed output is sorted (codes non-decreasing)
@@ -260,7 +407,7 @@ def run_gpu(args):
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
         key = f"{args.dtype}:{args.n}:{args.dist}"
-        if key in tr:
+        if key in tr and tr[key].get("kernel_hash") == kernel_hash():
             traffic = tr[key]["bytes_per_launch"]
     except Exception:  # noqa: BLE001
         pass
@@ -271,16 +418,18 @@ def run_gpu(args):
     gpu_launches = sum(v["launches"] for v in prof.values())
 
     # end to end through the public host-buffer entry point (copies inside)
-    e2e_times = []
-    pinned = torch.empty(src.numel() * src.element_size(), dtype=torch.uint8, pin_memory=True)
-    host_view = pinned.numpy().view(a.dtype).reshape(a.shape)
-    for _ in range(args.e2e_steps + 1):
-        host_view[...] = a
-        t0 = time.perf_counter()
-        vq.sort_host(host_view, args.dtype)
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_times = e2e_times[1:]
-    e2e_val = world * args.n * len(e2e_times) / sum(e2e_times) / 1e9
+    e2e_val = None
+    if not args.no_e2e:
+        e2e_times = []
+        pinned = torch.empty(src.numel() * src.element_size(), dtype=torch.uint8, pin_memory=True)
+        host_view = pinned.numpy().view(a.dtype).reshape(a.shape)
+        for _ in range(max(1, args.e2e_steps) + 1):
+            host_view[...] = a
+            t0 = time.perf_counter()
+            vq.sort_host(host_view, args.dtype)
+            e2e_times.append(time.perf_counter() - t0)
+        e2e_times = e2e_times[1:]
+        e2e_val = world * args.n * len(e2e_times) / sum(e2e_times) / 1e9
 
     line = {
         "metric": "sort throughput (GKeys/s), 1e8 keys per array",
@@ -301,13 +450,20 @@ def run_gpu(args):
                           "levels_run_keys": st["keys_partitioned"], "max_depth": st["max_depth"],
                           "leaf_ms_per_step": leaf_ms},
         "kernels": kernels,
+        "kernel_hash": kernel_hash(),
         "gpu_launches": gpu_launches,
         "e2e": {"value": e2e_val, "unit": "GKeys/s", "h2d_bytes_per_step": args.n * kb,
                 "d2h_bytes_per_step": args.n * kb, "path": "vqsort_sort_host (pinned host buffer)"},
         "clocks": clk,
     }
     if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(args, a, args.cpu_seconds)
+        if not args.no_extras:
+            del src
+            torch.cuda.empty_cache()
+            line["per_dtype"] = extra_dtypes(vq, torch, peak, args.n)
+            line["batched"] = extra_batched(vq, torch)
+            line["served"] = extra_served(vq, torch, args.served_requests)
+        line["cpu_baseline"] = None if args.no_cpu else cpu_baseline(args, a, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -194,9 +194,13 @@ typedef enum vq_option {
   VQ_OPT_SEED = 2,          /* seed of the per-range pivot sampling streams */
   VQ_OPT_SPIN_LIMIT = 3,    /* iterations of each bounded device wait (default 2^22,
                                about a second) */
-  VQ_OPT_TEST_STALL = 4     /* 1: the first tile never publishes its count, so the next
-                               tile's wait runs out and the sort reports VQ_ERR_TIMEOUT
-                               (test of the bounded-wait path; never hangs) */
+  VQ_OPT_TEST_STALL = 4,    /* 1: the root range never publishes its children, so every
+                               block's bounded wait for work runs out and the sort reports
+                               VQ_ERR_TIMEOUT (test of the bounded-wait path; never hangs) */
+  VQ_OPT_TILE_BYTES = 5,    /* 0 or 32768: 32 KiB partition tiles (default); 16384: 16 KiB */
+  VQ_OPT_LEAF_THREADS = 6   /* 0: block leaves use cutoff/16 threads (16 keys per thread);
+                               256, 512 or 1024: that many threads, so cutoff/threads keys
+                               per thread (at most 16); ignored for 16-byte keys */
 } vq_option;
 vq_status vqsort_set_option(vq_option opt, int64_t value);
 int64_t vqsort_get_option(vq_option opt);

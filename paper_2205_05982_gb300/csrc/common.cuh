@@ -54,6 +54,10 @@ __host__ __device__ __forceinline__ bool eq(const U128 &a, const U128 &b) {
 
 template <class C> __device__ __forceinline__ C cmin(const C &a, const C &b) { return lt(b, a) ? b : a; }
 template <class C> __device__ __forceinline__ C cmax(const C &a, const C &b) { return lt(b, a) ? a : b; }
+// 32-bit codes use the integer min/max instructions directly (64-bit ones
+// are slower than one compare and two selects).
+__device__ __forceinline__ uint32_t cmin(const uint32_t &a, const uint32_t &b) { return umin(a, b); }
+__device__ __forceinline__ uint32_t cmax(const uint32_t &a, const uint32_t &b) { return umax(a, b); }
 
 // Compare-and-exchange: a <- min, b <- max.
 template <class C> __device__ __forceinline__ void cas(C &a, C &b) {
@@ -317,6 +321,8 @@ struct SortArgs {
   unsigned long long seed;
   unsigned int cap_q, cap_segs, cap_leaf_warp, cap_leaf_block, cap_fb;
   unsigned int tile_keys;              // keys per partition tile
+  unsigned int tile_cpt;               // 16-byte chunks per thread of the partition tile window
+  unsigned int leaf_threads;           // threads of a block-leaf CTA (0: 16 keys per thread)
   unsigned int leaf_cutoff;            // ranges <= this go to the leaf kernels
   int depth_override;                  // < 0: 2*floor(log2 m)+4
   unsigned int spin_limit;

@@ -9,19 +9,27 @@
 
 namespace vq {
 
-// Partition kernel geometry: 256 threads, 8 chunks of 16 bytes per thread.
+// Partition kernel geometry: 256 threads, CPT chunks of 16 bytes per thread
+// (CPT = 8: 32 KiB tile windows, the default; CPT = 4: 16 KiB windows).
 constexpr int PART_NT = 256;
-constexpr int PART_CPT = 8;
-constexpr int PART_WINDOW = PART_NT * PART_CPT * 16;   // bytes of one tile window
-constexpr int PART_SMEM = PART_WINDOW + 128;           // tile window (+ slack, 128-byte aligned)
+constexpr int PART_CPT = 8;                            // default
 constexpr int PART_BLOCKS_PER_SM = 5;
+__host__ __device__ constexpr int part_window(int cpt) { return PART_NT * cpt * 16; }
+__host__ __device__ constexpr int part_smem(int cpt) { return part_window(cpt) + 128; }
 // Tile keys: the tile plus its 16-byte misalignment fits the window.
-__host__ __device__ constexpr unsigned part_tile_keys(int kb) { return (PART_WINDOW - 16) / kb; }
+__host__ __device__ constexpr unsigned part_tile_keys(int kb, int cpt = PART_CPT) {
+  return (unsigned)((part_window(cpt) - 16) / kb);
+}
 
 constexpr int LEAF_NT = 1024;       // threads of the block leaf kernel
 constexpr int FB_NT = 256;          // threads of the merge fallback kernel
 constexpr int FB_R = 8;             // keys per thread in its chunk sort
 constexpr int FB_CHUNK = FB_NT * FB_R;
+
+// Threads of a block-leaf CTA: 16 keys per thread at the cutoff unless set.
+__host__ constexpr int leaf_nt_for(unsigned cutoff, int threads) {
+  return threads ? threads : (cutoff >= 16384 ? 1024 : cutoff >= 8192 ? 512 : 256);
+}
 
 // Default and largest block-leaf cutoff (keys) per key size.
 __host__ constexpr unsigned default_leaf_cutoff(int kb) {

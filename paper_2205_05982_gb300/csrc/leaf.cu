@@ -132,9 +132,6 @@ template <int KB, int NT> __global__ void __launch_bounds__(NT, NT <= 512 ? 2 : 
   }
 }
 
-// Threads per block-leaf CTA for a cutoff: 16 keys per thread at the cutoff.
-constexpr int leaf_nt(unsigned cutoff) { return cutoff >= 16384 ? 1024 : cutoff >= 8192 ? 512 : 256; }
-
 template <int KB, int NT> int leaf_block_grid(size_t smem) {
   static int grid = 0;
   static size_t last = 0;
@@ -169,7 +166,7 @@ template <int KB> cudaError_t leaf_block_impl(const SortArgs &a, cudaStream_t s)
   if constexpr (KB == 16) {   // cutoff <= 4096: always 256 threads
     k_leaf_block<KB, 256><<<leaf_block_grid<KB, 256>(smem), 256, smem, s>>>(a);
   } else {
-    switch (leaf_nt(C)) {
+    switch (leaf_nt_for(C, a.leaf_threads)) {
       case 1024: k_leaf_block<KB, 1024><<<leaf_block_grid<KB, 1024>(smem), 1024, smem, s>>>(a); break;
       case 512: k_leaf_block<KB, 512><<<leaf_block_grid<KB, 512>(smem), 512, smem, s>>>(a); break;
       default: k_leaf_block<KB, 256><<<leaf_block_grid<KB, 256>(smem), 256, smem, s>>>(a); break;

@@ -108,6 +108,7 @@ extern "C" vq_status vqsort_partition_noalloc(vq_dtype dt, const void *d_in, voi
   a.cap_q = NOALLOC_TILES;
   a.cap_segs = 64;
   a.tile_keys = (unsigned)T;
+  a.tile_cpt = PART_CPT;
   a.leaf_cutoff = default_leaf_cutoff(kb);
   a.depth_override = -1;
   a.spin_limit = 1u << 22;

@@ -131,7 +131,7 @@ __device__ typename KT<KB>::Code sample_pivot(const void *buf, uint64_t b, uint6
 template <int KB>
 __device__ void make_segment(const SortArgs &a, uint64_t b, uint64_t e, unsigned depth, unsigned flags,
                              typename KT<KB>::Code pivot, unsigned depth_limit, RangeScratch &rs) {
-  constexpr unsigned T = part_tile_keys(KB);
+  const unsigned T = a.tile_keys;
   const uint64_t m = e - b;
   const unsigned nt = (unsigned)((m + T - 1) / T);
   if (threadIdx.x == 0) {
@@ -353,14 +353,14 @@ template <int KB> __device__ __forceinline__ typename KT<KB>::Mem to_mem(typenam
 // Pass 1 over the tile window: left keys (code <= pivot), valid keys, and
 // whether some key is < pivot. Chunks fully inside the tile skip the
 // per-key bounds test.
-template <int KB, bool RAW>
+template <int KB, int CPT, bool RAW>
 __device__ __forceinline__ void count_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
                                            unsigned hi, typename KT<KB>::Code piv, unsigned &nL,
                                            unsigned &nV, int &anyLt) {
   using C = typename KT<KB>::Code;
   constexpr unsigned V = 16 / KB;
 #pragma unroll 2
-  for (int j = 0; j < PART_CPT; ++j) {
+  for (int j = 0; j < CPT; ++j) {
     const unsigned c = threadIdx.x + j * NT;
     const uint4 q = c < nwc ? sw[c] : make_uint4(0, 0, 0, 0);
     const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
@@ -379,7 +379,7 @@ __device__ __forceinline__ void count_tile(const SortArgs &a, const uint4 *sw, u
 
 // Pass 2 over the tile window: every valid key goes to its ballot rank in
 // the left run (outL) or the right run (outR).
-template <int KB, bool RAW, bool DEC>
+template <int KB, int CPT, bool RAW, bool DEC>
 __device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
                                              unsigned hi, typename KT<KB>::Code piv,
                                              typename KT<KB>::Mem *outL, typename KT<KB>::Mem *outR,
@@ -389,7 +389,7 @@ __device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *sw,
   const unsigned lane = threadIdx.x & 31;
   const unsigned ltm = (1u << lane) - 1u;
 #pragma unroll 2
-  for (int j = 0; j < PART_CPT; ++j) {
+  for (int j = 0; j < CPT; ++j) {
     const unsigned c = threadIdx.x + j * NT;
     const uint4 q = c < nwc ? sw[c] : make_uint4(0, 0, 0, 0);
     const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
@@ -483,7 +483,7 @@ __device__ __forceinline__ void load_desc(const SortArgs &a, unsigned long long 
 template <int KB>
 __device__ __forceinline__ void issue_tile(const SortArgs &a, unsigned long long item, const SegDesc &seg,
                                            unsigned char *buf, uint64_t *bar) {
-  constexpr unsigned T = part_tile_keys(KB);
+  const unsigned T = a.tile_keys;
   const unsigned i = (unsigned)(item & 0xFFFFFFFFu);
   const uint64_t b = seg.begin, e = seg.end;
   const bool par = seg.flags & SEG_PARITY;
@@ -505,10 +505,10 @@ __device__ __forceinline__ void issue_tile(const SortArgs &a, unsigned long long
 // key straight from its ballot rank to global memory (each warp store is two
 // contiguous runs). A block needs only the window and few registers, so
 // several blocks per SM keep enough bytes in flight.
-template <int KB> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER_SM) k_partition(SortArgs a) {
+template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER_SM) k_partition(SortArgs a) {
   using C = typename KT<KB>::Code;
   using M = typename KT<KB>::Mem;
-  constexpr unsigned T = part_tile_keys(KB);
+  const unsigned T = a.tile_keys;   // <= part_tile_keys(KB, CPT)
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t s_bar;
   __shared__ SegDesc s_seg;
@@ -570,8 +570,8 @@ template <int KB> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER_SM) k_pa
     // ---- pass 1: per-warp counts of left and valid keys
     unsigned nL = 0, nV = 0;
     int anyLt = 0;
-    if (raw) count_tile<KB, true>(a, sw, nwc, lo, hi, piv, nL, nV, anyLt);
-    else count_tile<KB, false>(a, sw, nwc, lo, hi, piv, nL, nV, anyLt);
+    if (raw) count_tile<KB, CPT, true>(a, sw, nwc, lo, hi, piv, nL, nV, anyLt);
+    else count_tile<KB, CPT, false>(a, sw, nwc, lo, hi, piv, nL, nV, anyLt);
     nL = __reduce_add_sync(FULL, nL);
     nV = __reduce_add_sync(FULL, nV);
     if (lane == 0) {
@@ -610,9 +610,9 @@ template <int KB> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER_SM) k_pa
       M *outL = dst + b + (cur & 0xFFFFFFFFull);
       M *outR = dst + (e - (cur >> 32) - tileR);
       const unsigned runL = s_bL[warp], runR = s_bR[warp];
-      if (a.mode == MODE_PARTITION) scatter_tile<KB, true, true>(a, sw, nwc, lo, hi, piv, outL, outR, runL, runR);
-      else if (raw) scatter_tile<KB, true, false>(a, sw, nwc, lo, hi, piv, outL, outR, runL, runR);
-      else scatter_tile<KB, false, false>(a, sw, nwc, lo, hi, piv, outL, outR, runL, runR);
+      if (a.mode == MODE_PARTITION) scatter_tile<KB, CPT, true, true>(a, sw, nwc, lo, hi, piv, outL, outR, runL, runR);
+      else if (raw) scatter_tile<KB, CPT, true, false>(a, sw, nwc, lo, hi, piv, outL, outR, runL, runR);
+      else scatter_tile<KB, CPT, false, false>(a, sw, nwc, lo, hi, piv, outL, outR, runL, runR);
     }
     fence_proxy_async_smem();   // the next TMA copy reuses the window
     __syncthreads();
@@ -640,14 +640,14 @@ template <int KB> __global__ void __launch_bounds__(NT) k_choose_pivot(SortArgs 
   if (threadIdx.x == 0) store_key<KB>(out, 0, decode<KB>(p, a.codec));
 }
 
-template <int KB> int partition_grid() {
+template <int KB, int CPT> int partition_grid() {
   static int grid = 0;
   if (!grid) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_partition<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, PART_SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_partition<KB>, NT, PART_SMEM);
+    cudaFuncSetAttribute(k_partition<KB, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, part_smem(CPT));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_partition<KB, CPT>, NT, part_smem(CPT));
     grid = sms * (per > 0 ? per : 1);
   }
   return grid;
@@ -660,7 +660,11 @@ template <int KB> cudaError_t seed_impl(const SortArgs &a, cudaStream_t s) {
 }
 
 template <int KB> cudaError_t partition_impl(const SortArgs &a, cudaStream_t s) {
-  k_partition<KB><<<partition_grid<KB>(), NT, PART_SMEM, s>>>(a);
+  if (a.tile_cpt == 4) {
+    k_partition<KB, 4><<<partition_grid<KB, 4>(), NT, part_smem(4), s>>>(a);
+  } else {
+    k_partition<KB, 8><<<partition_grid<KB, 8>(), NT, part_smem(8), s>>>(a);
+  }
   return cudaGetLastError();
 }
 

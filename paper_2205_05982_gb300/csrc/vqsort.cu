@@ -52,6 +52,13 @@ int64_t g_leaf_cutoff = 0;
 int64_t g_seed = 0x22050598;
 int64_t g_spin_limit = 1 << 22;
 int64_t g_test_stall = 0;
+int64_t g_tile_bytes = 0;     // 0: 32 KiB partition tile windows
+int64_t g_leaf_threads = 0;   // 0: 16 keys per thread at the cutoff
+
+int tile_cpt() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_tile_bytes == 16384 ? 4 : 8;
+}
 
 unsigned leaf_cutoff_for(int kb) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -70,8 +77,9 @@ struct Layout {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_limit, bool with_alt) {
-  const uint64_t T = part_tile_keys(kb);
+Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_limit, bool with_alt,
+                   int cpt) {
+  const uint64_t T = part_tile_keys(kb, cpt);
   const uint64_t lg = floor_log2_u64(n < 2 ? 2 : n);
   uint64_t levels = 2 * lg + 4;
   if (depth_limit >= 0 && (uint64_t)depth_limit > levels) levels = (uint64_t)depth_limit;
@@ -228,16 +236,18 @@ struct Job {
 vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   const int kb = key_bytes(j.dt);
   const unsigned C = leaf_cutoff_for(kb);
-  int64_t depth_limit, seed, spin, stall;
+  int64_t depth_limit, seed, spin, stall, leaf_threads;
+  const int cpt = j.mode == MODE_SORT ? tile_cpt() : PART_CPT;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     depth_limit = g_depth_limit;
     seed = g_seed;
     spin = g_spin_limit;
     stall = g_test_stall;
+    leaf_threads = g_leaf_threads;
   }
   const bool with_alt = j.mode == MODE_SORT;
-  const Layout L = make_layout(kb, j.n, j.num_segments, C, depth_limit, with_alt);
+  const Layout L = make_layout(kb, j.n, j.num_segments, C, depth_limit, with_alt, cpt);
   if (!ws || ws_bytes < L.total) return VQ_ERR_NOMEM;
   if ((uintptr_t)ws & 255) return VQ_ERR_INVALID;
   unsigned char *w = (unsigned char *)ws;
@@ -260,7 +270,9 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   a.cap_leaf_warp = L.cap_lw;
   a.cap_leaf_block = L.cap_lb;
   a.cap_fb = L.cap_fb;
-  a.tile_keys = part_tile_keys(kb);
+  a.tile_keys = part_tile_keys(kb, cpt);
+  a.tile_cpt = (unsigned)cpt;
+  a.leaf_threads = kb == 16 ? 0u : (unsigned)leaf_threads;
   a.leaf_cutoff = C;
   a.depth_override = (int)depth_limit;
   a.spin_limit = (unsigned)spin;
@@ -313,7 +325,7 @@ vq_status sort_common(vq_dtype dt, void *keys, uint64_t n, const uint64_t *offse
       std::lock_guard<std::mutex> lk(g_mu);
       dl = g_depth_limit;
     }
-    const Layout L = make_layout(kb, n, offsets ? S : 1, leaf_cutoff_for(kb), dl, true);
+    const Layout L = make_layout(kb, n, offsets ? S : 1, leaf_cutoff_for(kb), dl, true, tile_cpt());
     if ((st = owned_ws(s, L.total, &ws, &ws_bytes)) != VQ_OK) return st;
   }
   Job j{dt, keys, nullptr, n, offsets, offsets ? S : 1, asc, MODE_SORT, nullptr, nullptr};
@@ -363,7 +375,7 @@ size_t vqsort_workspace_bytes(vq_dtype dt, size_t n_total, size_t num_segments) 
     std::lock_guard<std::mutex> lk(g_mu);
     dl = g_depth_limit;
   }
-  return make_layout(kb, n_total, num_segments ? num_segments : 1, leaf_cutoff_for(kb), dl, true).total;
+  return make_layout(kb, n_total, num_segments ? num_segments : 1, leaf_cutoff_for(kb), dl, true, 4).total;
 }
 
 vq_status vqsort_sort_ws(vq_dtype dt, void *d_keys, size_t n, int ascending, void *d_ws, size_t ws_bytes,
@@ -421,7 +433,7 @@ vq_status vqsort_partition(vq_dtype dt, const void *d_in, void *d_out, size_t n,
   if ((st = check_device()) != VQ_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const int kb = key_bytes(dt);
-  const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb), -1, false);
+  const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb), -1, false, PART_CPT);
   void *ws;
   size_t wsb;
   if ((st = owned_ws(s, L.total, &ws, &wsb)) != VQ_OK) return st;
@@ -502,6 +514,14 @@ vq_status vqsort_set_option(vq_option opt, int64_t value) {
       g_spin_limit = value;
       return VQ_OK;
     case VQ_OPT_TEST_STALL: g_test_stall = value ? 1 : 0; return VQ_OK;
+    case VQ_OPT_TILE_BYTES:
+      if (value != 0 && value != 16384 && value != 32768) return VQ_ERR_INVALID;
+      g_tile_bytes = value;
+      return VQ_OK;
+    case VQ_OPT_LEAF_THREADS:
+      if (value != 0 && value != 256 && value != 512 && value != 1024) return VQ_ERR_INVALID;
+      g_leaf_threads = value;
+      return VQ_OK;
   }
   return VQ_ERR_INVALID;
 }
@@ -514,6 +534,8 @@ int64_t vqsort_get_option(vq_option opt) {
     case VQ_OPT_SEED: return g_seed;
     case VQ_OPT_SPIN_LIMIT: return g_spin_limit;
     case VQ_OPT_TEST_STALL: return g_test_stall;
+    case VQ_OPT_TILE_BYTES: return g_tile_bytes;
+    case VQ_OPT_LEAF_THREADS: return g_leaf_threads;
   }
   return -1;
 }

@@ -1,0 +1,87 @@
+"""Host-side logic that needs no GPU: request generation and statistics of
+the serving loop, tuning candidates, and the multi-rank timing reduction of
+bench.py on two gloo ranks."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+
+class FakeSource:
+    def __init__(self, n):
+        self.shape = (n,)
+
+
+def test_poisson_requests_shape():
+    from paper_2205_05982_gb300 import serve
+    src = {dt: FakeSource(10**7) for dt in ("i16", "u32", "f32", "u64", "kv64")}
+    reqs = serve.poisson_requests(5000, 1000.0, src, seed=1)
+    sizes = np.array([r.n for r in reqs])
+    assert sizes.min() >= 1000 and sizes.max() <= 10**7
+    # log-uniform: about half the requests below the geometric midpoint 1e5
+    assert 0.45 < (sizes < 10**5).mean() < 0.55
+    arr = np.array([r.arrival for r in reqs])
+    assert arr[0] == 0 and (np.diff(arr) >= 0).all()
+    assert abs(np.diff(arr).mean() - 1e-3) < 1e-4            # rate 1000/s
+    kinds = {dt: sum(r.dtype == dt for r in reqs) for dt in src}
+    assert min(kinds.values()) > 800
+    assert all(0 <= r.offset <= 10**7 - r.n for r in reqs)
+
+
+def test_summarize():
+    from paper_2205_05982_gb300 import serve
+    reqs = []
+    for i in range(100):
+        r = serve.Request(i, i * 0.001, "u32", 1000, None)
+        r.done_ms = i + 2.0
+        r.latency_ms = 2.0 + (i % 10)
+        reqs.append(r)
+    s = serve.summarize(reqs)
+    assert s["requests"] == 100 and s["keys"] == 100_000
+    assert s["p50_ms"] == pytest.approx(6.5) and s["p99_ms"] == pytest.approx(11.0)
+    assert s["span_ms"] == pytest.approx(101.0 - 0.0)
+
+
+def test_tuning_candidates_valid():
+    from paper_2205_05982_gb300 import batch
+    for dt in ("u16", "u32", "u64", "u128"):
+        c = batch.candidates(dt)
+        assert c
+        for x in c:
+            assert x["tile_bytes"] in (16384, 32768)
+            if x["leaf_threads"]:
+                assert 1 <= x["leaf_cutoff"] // x["leaf_threads"] <= 16
+            if dt == "u128":
+                assert x["leaf_cutoff"] <= 4096 and x["leaf_threads"] == 0
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    got = bench.max_over_ranks(10.0 + rank, dist)
+    q.put((rank, got))
+    dist.destroy_process_group()
+
+
+def test_bench_takes_max_over_two_gloo_ranks():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(120)
+        assert p.exitcode == 0
+    res = dict(q.get(timeout=10) for _ in range(2))
+    assert res == {0: 11.0, 1: 11.0}
