@@ -196,6 +196,15 @@ __device__ __forceinline__ void st_release(unsigned long long *p, uint64_t v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"((unsigned long long)v) : "memory");
 }
 
+// Release add (orders this thread's earlier writes, and those it has observed
+// through a block barrier, before the add) returning the old value.
+__device__ __forceinline__ uint32_t atom_add_release(unsigned int *p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }

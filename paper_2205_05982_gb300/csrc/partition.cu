@@ -511,8 +511,9 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
   const unsigned T = a.tile_keys;   // <= part_tile_keys(KB, CPT)
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t s_bar;
-  __shared__ SegDesc s_seg;
-  __shared__ unsigned long long s_item;
+  __shared__ SegDesc s_seg, s_fseg;
+  __shared__ unsigned long long s_item, s_ticket;
+  __shared__ unsigned s_fsid;
   __shared__ int s_go, s_fin;
   __shared__ unsigned s_wL[NWARP], s_wV[NWARP], s_bL[NWARP], s_bR[NWARP];
   __shared__ unsigned long long s_cur;
@@ -526,20 +527,63 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
   }
   __syncthreads();
   uint32_t phase = 0;
+  // Thread 0 state: the range whose descriptor is in s_seg, and the
+  // completion count of the previous tile, read one claim later so that the
+  // two round trips overlap.
+  unsigned seg_in_smem = ~0u, pend_sid = ~0u, pend_nt = 0;
+  uint32_t pend_prev = 0;
 
   for (;;) {
     if (tid == 0) {
+      const unsigned long long t = atomicAdd(&a.hdr->head, 1ull);
       unsigned long long item = 0;
-      const int go = claim(a, item);
-      s_go = go;
-      if (go) {
+      const bool have = probe_ticket(a, t, item);
+      int fin = 0;
+      if (pend_sid != ~0u) {
+        fin = pend_prev == pend_nt - 1;
+        if (fin) {
+          fence_acquire();
+          s_fsid = pend_sid;
+          load_desc(a, (unsigned long long)pend_sid << 32, s_fseg);
+        }
+        pend_sid = ~0u;
+      }
+      s_fin = fin;
+      if (have) {
         s_item = item;
-        load_desc(a, item, s_seg);
+        const unsigned sid = (unsigned)((item >> 32) & 0x7FFFFFFFu);
+        if (sid != seg_in_smem) {
+          load_desc(a, item, s_seg);
+          seg_in_smem = sid;
+        }
         issue_tile<KB>(a, item, s_seg, smem, &s_bar);
       }
+      s_go = have;
+      s_ticket = t;
     }
     __syncthreads();
-    if (!s_go) break;
+    // the previous tile finished its range: the rest of Algorithm 1 for it
+    if (s_fin) finish_range<KB>(a, s_fseg, s_fsid, s_sample, rs);
+    if (!s_go) {
+      // the claimed item is not published yet (it may come from the range
+      // just finished above): wait for it
+      if (tid == 0) {
+        unsigned long long item = 0;
+        const int go = wait_ticket(a, s_ticket, item);
+        if (go) {
+          s_item = item;
+          const unsigned sid = (unsigned)((item >> 32) & 0x7FFFFFFFu);
+          if (sid != seg_in_smem) {
+            load_desc(a, item, s_seg);
+            seg_in_smem = sid;
+          }
+          issue_tile<KB>(a, item, s_seg, smem, &s_bar);
+        }
+        s_go = go;
+      }
+      __syncthreads();
+      if (!s_go) break;
+    }
     {
       unsigned it = 0;
       while (!mbar_try_wait(&s_bar, phase)) {
@@ -617,17 +661,14 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
     fence_proxy_async_smem();   // the next TMA copy reuses the window
     __syncthreads();
 
-    // ---- range completion: one release/acquire by thread 0 covers the
-    // whole block's stores (ordered before it by the barrier)
+    // ---- range completion: one release add by thread 0 covers the whole
+    // block's stores (ordered before it by the barrier above); its result is
+    // read after the next claim
     if (tid == 0) {
-      __threadfence();
-      const unsigned prev = atomicAdd(&a.segs[sid].tiles_done, 1u);
-      const int fin = prev == sg.ntiles - 1;
-      if (fin) __threadfence();
-      s_fin = fin;
+      pend_prev = atom_add_release(&a.segs[sid].tiles_done, 1u);
+      pend_sid = sid;
+      pend_nt = sg.ntiles;
     }
-    __syncthreads();
-    if (s_fin) finish_range<KB>(a, sg, sid, s_sample, rs);
   }
 }
 
