@@ -165,7 +165,8 @@ vq_status vqsort_last_device_status(const void *d_ws, void *stream);
 
 /* Counters of the last sort on a workspace (waits for `stream`). */
 typedef struct vq_stats {
-  uint64_t keys_partitioned;     /* sum over partition levels of keys read+written once */
+  uint64_t keys_partitioned;     /* sum over partition levels (two-way and K-way) of keys
+                                    read once and written once */
   uint64_t tiles;                /* partition tiles processed */
   uint64_t segments;             /* ranges partitioned */
   uint64_t leaves_warp;          /* ranges of <= 512 keys sorted by one warp */
@@ -178,6 +179,10 @@ typedef struct vq_stats {
   uint64_t fallback_keys;
   uint64_t max_depth;            /* deepest partition level reached */
   uint64_t device_status;        /* vq_status latched on the device */
+  uint64_t keys_counted;         /* keys read by K-way counting passes */
+  uint64_t kway_ranges;          /* ranges split 16 ways */
+  uint64_t guard;                /* first failed device bounds guard (0: none); a failed guard
+                                    skips the access and latches VQ_ERR_INTERNAL */
 } vq_stats;
 vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out);
 
@@ -198,9 +203,13 @@ typedef enum vq_option {
                                block's bounded wait for work runs out and the sort reports
                                VQ_ERR_TIMEOUT (test of the bounded-wait path; never hangs) */
   VQ_OPT_TILE_BYTES = 5,    /* 0 or 32768: 32 KiB partition tiles (default); 16384: 16 KiB */
-  VQ_OPT_LEAF_THREADS = 6   /* 0: block leaves use cutoff/16 threads (16 keys per thread);
+  VQ_OPT_LEAF_THREADS = 6,  /* 0: block leaves use cutoff/16 threads (16 keys per thread);
                                256, 512 or 1024: that many threads, so cutoff/threads keys
                                per thread (at most 16); ignored for 16-byte keys */
+  VQ_OPT_KWAY = 7           /* 1 (default): ranges of >= 2^18 keys are split 16 ways per
+                               level (15 sampled splitters, a counting pass and a scatter
+                               pass; the K > 2 partition of Sec. 4.2); 0: every level is the
+                               paper's two-way Partition. The output is the same. */
 } vq_option;
 vq_status vqsort_set_option(vq_option opt, int64_t value);
 int64_t vqsort_get_option(vq_option opt);

@@ -269,7 +269,11 @@ struct Header {
   unsigned long long leaves_warp, leaves_block, leaf_keys;
   unsigned long long equal_ranges, equal_keys, degenerate;
   unsigned long long fallback_ranges, fallback_keys, max_depth;
-  unsigned long long pad[7];
+  unsigned long long nkw;          // K-way range records allocated
+  unsigned long long keys_counted; // keys read by K-way counting passes (statistics)
+  unsigned long long kway_ranges;  // ranges split K ways (statistics)
+  unsigned long long guard;        // first failed bounds guard (GUARD_*), 0 if none
+  unsigned long long pad[3];
 };
 static_assert(sizeof(Header) % 64 == 0, "header size");
 
@@ -292,6 +296,8 @@ enum : unsigned int {
   SEG_PARITY = 1u,   // keys live in the alternate buffer (else the user buffer)
   SEG_RAW = 2u,      // keys are still in input form (root ranges)
   SEG_EXCL = 4u,     // pivot is one below a repeated maximum: right side all equal
+  SEG_KWAY = 16u,    // split KWAY ways by the splitters of K-way record piv_lo
+  SEG_NOKWAY = 32u,  // a K-way split made no progress here: split in two
 };
 
 // A range handed to the leaf or fallback kernels.
@@ -302,8 +308,23 @@ struct LeafEntry {
 };
 enum : unsigned int { LEAF_COPY = 8u };   // all keys equal: decode and copy only
 
-// Work-queue item: bit 63 valid, bits 32..62 segment id, bits 0..31 tile.
+// Work-queue item: bit 63 valid, bits 32..62 segment id, bit 31 phase (K-way
+// ranges: 0 = counting pass, 1 = scatter pass), bits 0..30 tile.
 constexpr unsigned long long ITEM_VALID = 1ull << 63;
+constexpr unsigned long long ITEM_PHASE = 1ull << 31;
+
+// K-way levels (samplesort-style multi-pivot partition for large ranges).
+constexpr unsigned KWAY = 16;              // buckets per K-way level
+constexpr unsigned KWAY_SAMPLE = 512;      // keys in the splitter sample
+constexpr unsigned long long KWAY_MIN = 1ull << 18;   // smallest range split K ways
+
+// Splitters and per-bucket counters of one K-way range.
+struct KwayDesc {
+  unsigned long long split_lo[KWAY], split_hi[KWAY];   // KWAY-1 splitter codes (ascending)
+  unsigned long long count[KWAY];    // counting pass: keys per bucket (atomic)
+  unsigned long long cursor[KWAY];   // scatter pass: next free slot per bucket (atomic)
+  unsigned long long start[KWAY + 1];// bucket bounds (key indices), set between the passes
+};
 
 // Warp leaves handle ranges up to this many keys (32 lanes x 16 keys).
 constexpr unsigned WARP_LEAF_MAX = 512;
@@ -323,12 +344,13 @@ struct SortArgs {
   SegDesc *segs;
   unsigned long long *items;
   LeafEntry *leaf_warp, *leaf_block, *fb;
+  KwayDesc *kw;                        // K-way range records (null: K-way levels off)
   const unsigned long long *offsets;   // CSR offsets or null (one segment)
   unsigned long long n_total;
   unsigned long long num_segments;
   unsigned long long *out_left;        // MODE_PARTITION result
   unsigned long long seed;
-  unsigned int cap_q, cap_segs, cap_leaf_warp, cap_leaf_block, cap_fb;
+  unsigned int cap_q, cap_segs, cap_leaf_warp, cap_leaf_block, cap_fb, cap_kw;
   unsigned int tile_keys;              // keys per partition tile
   unsigned int tile_cpt;               // 16-byte chunks per thread of the partition tile window
   unsigned int leaf_threads;           // threads of a block-leaf CTA (0: 16 keys per thread)
@@ -365,6 +387,20 @@ __host__ __device__ __forceinline__ uint64_t range_seed(uint64_t seed, uint64_t 
 __device__ __forceinline__ void raise_error(const SortArgs &a, unsigned code) {
   atomicCAS(&a.hdr->error, 0ull, (unsigned long long)code);
   st_release(&a.hdr->abort, 1);
+}
+
+// Bounds guards: a failed guard skips the access it protects, latches
+// VQ_ERR_INTERNAL and records which guard failed first.
+enum : unsigned {
+  GUARD_TILE = 1,       // a tile index past its range
+  GUARD_BINARY = 2,     // a two-way tile's reserved slots overflow its range
+  GUARD_BUCKET = 3,     // a K-way tile's reserved slots overflow a bucket
+  GUARD_BOUNDS = 4,     // K-way bucket bounds outside their range
+  GUARD_LEAF = 5,       // a leaf or fallback entry outside the array
+};
+__device__ __forceinline__ void guard_failed(const SortArgs &a, unsigned which) {
+  atomicCAS(&a.hdr->guard, 0ull, (unsigned long long)which);
+  raise_error(a, 6);
 }
 
 __device__ __forceinline__ bool aborted(const SortArgs &a) { return ld_relaxed(&a.hdr->abort) != 0; }

@@ -56,6 +56,10 @@ template <int KB> __global__ void __launch_bounds__(FB_NT) k_fallback(SortArgs a
   for (unsigned long long f = 0; f < nfb; ++f) {
     const LeafEntry le = a.fb[f];
     const uint64_t b = le.begin, len = le.len;
+    if (b + len > a.n_total) {   // guard (uniform across the grid)
+      if (blockIdx.x == 0 && threadIdx.x == 0) guard_failed(a, GUARD_LEAF);
+      return;
+    }
     const unsigned par = le.flags & SEG_PARITY;
     const bool raw = le.flags & SEG_RAW;
     void *bufA = (void *)buf_of<KB>(a, par), *bufB = (void *)buf_of<KB>(a, par ^ 1u);

@@ -59,6 +59,10 @@ template <int KB> __global__ void __launch_bounds__(256) k_leaf_warp(SortArgs a)
     idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
     if (idx >= n) break;
     const LeafEntry le = a.leaf_warp[idx];
+    if (le.begin + le.len > a.n_total || le.len > WARP_LEAF_MAX) {   // guard
+      if (lane == 0) guard_failed(a, GUARD_LEAF);
+      continue;
+    }
     const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
     const bool raw = le.flags & SEG_RAW;
     const unsigned len = le.len;
@@ -114,6 +118,10 @@ template <int KB, int NT> __global__ void __launch_bounds__(NT, NT <= 512 ? 2 : 
     __syncthreads();
     if (idx >= n) break;
     const LeafEntry le = a.leaf_block[idx];
+    if (le.begin + le.len > a.n_total || le.len > 16u * NT) {   // guard
+      if (threadIdx.x == 0) guard_failed(a, GUARD_LEAF);
+      continue;
+    }
     const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
     const bool raw = le.flags & SEG_RAW;
     const unsigned len = le.len;

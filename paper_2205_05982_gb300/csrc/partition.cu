@@ -228,13 +228,118 @@ __device__ void emit_fallback(const SortArgs &a, uint64_t b, uint64_t m, unsigne
   }
 }
 
+// ---------------------------------------------------------------------------
+// K-way ranges (the paper's K > 2 partition, Sec. 4.2, taken further on the
+// GPU): KWAY-1 splitters from a 512-key sample; a counting pass over the
+// range's tiles builds the bucket histogram, a scatter pass writes every key
+// to its bucket. Keys equal to a splitter go to the lower bucket (the "<="
+// rule of the binary partition).
+// ---------------------------------------------------------------------------
+
+// Samples KWAY_SAMPLE keys of [b, b+m) (64-byte chunks drawn as in
+// sample_pivot), sorts them with the block network and writes the splitters
+// (ranks 32j-1, j = 1..KWAY-1) to `split` (shared). Returns false when the
+// sample holds a single value (the binary path handles such ranges).
+template <int KB>
+__device__ bool sample_splitters(const void *buf, uint64_t b, uint64_t m, bool raw, Codec cd, uint64_t seed,
+                                 void *scratch, typename KT<KB>::Code *split) {
+  using C = typename KT<KB>::Code;
+  constexpr unsigned kc = 64 / KB, ns = KWAY_SAMPLE / kc;
+  constexpr unsigned R = KWAY_SAMPLE / NT;   // 2 keys per thread
+  static_assert(R * NT == KWAY_SAMPLE, "sample layout");
+  C *sx = (C *)scratch;
+  unsigned long long *s_chunk = (unsigned long long *)(sx + KWAY_SAMPLE);
+  __shared__ int s_same;
+  const uintptr_t addr = (uintptr_t)buf + b * KB;
+  const uint64_t off = ((64 - (addr & 63)) & 63) / KB;
+  const uint64_t nc = (m - off) / kc;
+  if (threadIdx.x == 0) {
+    Sfc64 r;
+    sfc_seed(r, seed);
+    for (unsigned j = 0; j < ns; ++j) s_chunk[j] = __umul64hi(sfc_next(r), nc);
+  }
+  __syncthreads();
+  C k[R];
+#pragma unroll
+  for (unsigned r = 0; r < R; ++r) {
+    const unsigned i = threadIdx.x + r * NT;
+    C c = load_cg<KB>(buf, b + off + s_chunk[i / kc] * kc + i % kc);
+    k[r] = raw ? encode<KB>(c, cd) : c;
+  }
+  group_sort<C, R, NT>(k, threadIdx.x, sx);
+  // thread t holds sorted ranks 2t, 2t+1
+  if (threadIdx.x % 16 == 15 && threadIdx.x < NT - 1) split[threadIdx.x / 16] = k[1];
+  if (threadIdx.x == 0) sx[0] = k[0];
+  __syncthreads();
+  if (threadIdx.x == NT - 1) s_same = eq(sx[0], k[R - 1]);
+  __syncthreads();
+  const bool ok = !s_same;
+  __syncthreads();
+  return ok;
+}
+
+// Creates a K-way range with the splitters in `split` (shared) and publishes
+// its counting-pass tiles.
+template <int KB>
+__device__ void make_kway_segment(const SortArgs &a, uint64_t b, uint64_t e, unsigned depth, unsigned flags,
+                                  unsigned depth_limit, const typename KT<KB>::Code *split, RangeScratch &rs) {
+  const unsigned T = a.tile_keys;
+  const uint64_t m = e - b;
+  const unsigned nt = (unsigned)((m + T - 1) / T);
+  __shared__ unsigned long long s_kid;
+  if (threadIdx.x == 0) {
+    const unsigned long long sid = atomicAdd(&a.hdr->nseg, 1ull);
+    const unsigned long long kid = atomicAdd(&a.hdr->nkw, 1ull);
+    const unsigned long long q0 = atomicAdd(&a.hdr->tail, (unsigned long long)nt);
+    const int ok = sid < a.cap_segs && kid < a.cap_kw && q0 + nt <= a.cap_q && sid < (1ull << 31);
+    if (ok) {
+      SegDesc &d = a.segs[sid];
+      d.begin = b;
+      d.end = e;
+      d.piv_lo = kid;
+      d.piv_hi = 0;
+      d.cursor = 0;
+      d.depth = depth;
+      d.flags = flags | SEG_KWAY;
+      d.ntiles = nt;
+      d.tiles_done = 0;
+      d.has_lt = 0;
+      d.depth_limit = depth_limit;
+    } else {
+      raise_error(a, ERR_INTERNAL);
+    }
+    rs.sid = sid;
+    rs.q0 = q0;
+    rs.ok = ok;
+    s_kid = kid;
+  }
+  __syncthreads();
+  if (rs.ok) {
+    KwayDesc &kw = a.kw[s_kid];
+    for (unsigned j = threadIdx.x; j < KWAY; j += blockDim.x) {
+      uint64_t lo = 0, hi = 0;
+      if (j < KWAY - 1) code_words<KB>(split[j], lo, hi);
+      kw.split_lo[j] = lo;
+      kw.split_hi[j] = hi;
+      kw.count[j] = 0;
+      kw.cursor[j] = 0;
+    }
+    __syncthreads();
+    const unsigned long long q0 = rs.q0, sid = rs.sid;
+    for (unsigned k = threadIdx.x; k < nt; k += blockDim.x)
+      st_release(&a.items[q0 + k], ITEM_VALID | (sid << 32) | k);
+  }
+  __syncthreads();
+}
+
 // A child of a partitioned range: leaf, fallback, or a new range to
 // partition (Algorithm 1: BaseCase for small sides, ChoosePivot + Recurse
 // otherwise; the depth bound of Sec. 2.2 before recursing). Returns the keys
 // handed to a leaf list or the fallback.
 template <int KB>
 __device__ uint64_t child_range(const SortArgs &a, uint64_t b, uint64_t e, unsigned depth, unsigned parity,
-                                unsigned depth_limit, void *scratch, RangeScratch &rs) {
+                                unsigned depth_limit, void *scratch, RangeScratch &rs, bool allow_kway = true) {
+  using C = typename KT<KB>::Code;
   const uint64_t m = e - b;
   if (m == 0) return 0;
   if (m <= a.leaf_cutoff) {
@@ -246,9 +351,79 @@ __device__ uint64_t child_range(const SortArgs &a, uint64_t b, uint64_t e, unsig
     return m;
   }
   const void *buf = parity ? a.alt : a.keys;
-  const auto p = sample_pivot<KB>(buf, b, m, false, a.codec, range_seed(a.seed, b, depth), scratch);
-  make_segment<KB>(a, b, e, depth, parity, p, depth_limit, rs);
+  const uint64_t seed = range_seed(a.seed, b, depth);
+  if (allow_kway && a.kw && m >= KWAY_MIN) {
+    C *split = (C *)((unsigned char *)scratch + KWAY_SAMPLE * sizeof(C) + 1024);
+    if (sample_splitters<KB>(buf, b, m, false, a.codec, seed, scratch, split)) {
+      make_kway_segment<KB>(a, b, e, depth, parity, depth_limit, split, rs);
+      return 0;
+    }
+  }
+  const auto p = sample_pivot<KB>(buf, b, m, false, a.codec, seed, scratch);
+  make_segment<KB>(a, b, e, depth, parity | (allow_kway ? 0u : SEG_NOKWAY), p, depth_limit, rs);
   return 0;
+}
+
+// After the counting pass of a K-way range: bucket bounds from the counts,
+// then the scatter-pass tiles.
+__device__ void finish_kway_count(const SortArgs &a, const SegDesc &sd, unsigned sid, RangeScratch &rs) {
+  KwayDesc &kw = a.kw[sd.piv_lo];
+  if (threadIdx.x == 0) {
+    unsigned long long pos = sd.begin;
+    for (unsigned j = 0; j < KWAY; ++j) {
+      kw.start[j] = pos;
+      kw.cursor[j] = pos;
+      pos += ld_relaxed(&kw.count[j]);
+    }
+    kw.start[KWAY] = pos;   // == sd.end
+    a.segs[sid].tiles_done = 0;
+    atomicAdd(&a.hdr->keys_counted, sd.end - sd.begin);
+    const unsigned long long q0 = atomicAdd(&a.hdr->tail, (unsigned long long)sd.ntiles);
+    rs.q0 = q0;
+    rs.ok = q0 + sd.ntiles <= a.cap_q;
+    if (!rs.ok) raise_error(a, ERR_INTERNAL);
+  }
+  __syncthreads();
+  if (rs.ok) {
+    const unsigned long long q0 = rs.q0;
+    for (unsigned k = threadIdx.x; k < sd.ntiles; k += blockDim.x)
+      st_release(&a.items[q0 + k], ITEM_VALID | ((unsigned long long)sid << 32) | ITEM_PHASE | k);
+  }
+  __syncthreads();
+}
+
+// After the scatter pass of a K-way range: its KWAY buckets are the children.
+template <int KB>
+__device__ void finish_kway_scatter(const SortArgs &a, const SegDesc &sd, unsigned sid, void *scratch,
+                                    RangeScratch &rs) {
+  if (a.test_stall && sid == 0) return;   // test hook: children never appear
+  const KwayDesc &kw = a.kw[sd.piv_lo];
+  const unsigned parity = (sd.flags & SEG_PARITY) ^ 1u;
+  const unsigned d1 = sd.depth + 1;
+  const uint64_t m = sd.end - sd.begin;
+  if (threadIdx.x == 0) {
+    atomicAdd(&a.hdr->keys_partitioned, m);
+    atomicAdd(&a.hdr->tiles, 2ull * sd.ntiles);
+    atomicAdd(&a.hdr->segments, 1ull);
+    atomicAdd(&a.hdr->kway_ranges, 1ull);
+    atomicMax(&a.hdr->max_depth, (unsigned long long)d1);
+  }
+  if (__ldcg(&kw.start[0]) != sd.begin || __ldcg(&kw.start[KWAY]) != sd.end) {   // guard
+    if (threadIdx.x == 0) guard_failed(a, GUARD_BOUNDS);
+    return;
+  }
+  uint64_t handed = 0;
+  for (unsigned j = 0; j < KWAY; ++j) {
+    const uint64_t cb = __ldcg(&kw.start[j]), ce = __ldcg(&kw.start[j + 1]);
+    if (ce < cb) {
+      if (threadIdx.x == 0) guard_failed(a, GUARD_BOUNDS);
+      break;
+    }
+    // a bucket holding the whole range made no progress: split it in two
+    handed += child_range<KB>(a, cb, ce, d1, parity, sd.depth_limit, scratch, rs, ce - cb < m);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && handed) atomicAdd(&a.hdr->remaining, (unsigned long long)(0ull - handed));
 }
 
 // Everything Algorithm 1 does after Partition returned, for range `sd`.
@@ -412,6 +587,96 @@ __device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *sw,
   }
 }
 
+// Bucket of a code among the KWAY-1 ascending splitters: the number of
+// splitters strictly below it (keys equal to a splitter take the lower bucket).
+template <class C> __device__ __forceinline__ unsigned bucket_of(const C &k, const C *split) {
+  unsigned bk = 0;
+#pragma unroll
+  for (unsigned step = KWAY / 2; step; step >>= 1)
+    if (lt(split[bk + step - 1], k)) bk += step;
+  return bk;
+}
+
+// One tile of a K-way range. Pass A: per-warp bucket counts (warp-aggregated
+// with __match_any_sync). Counting pass: add the tile's counts to the range's
+// histogram. Scatter pass: reserve the tile's slots in every bucket, then
+// write each key to bucket cursor + warp offset + rank among equal-bucket
+// lanes.
+template <int KB, int CPT, bool RAW>
+__device__ __forceinline__ void kway_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
+                                          unsigned hi, const typename KT<KB>::Code *split, bool scatter,
+                                          KwayDesc &kw, typename KT<KB>::Mem *dst, unsigned *s_wh,
+                                          unsigned long long *s_base) {
+  using C = typename KT<KB>::Code;
+  constexpr unsigned V = 16 / KB;
+  const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned ltm = (1u << lane) - 1u;
+  unsigned *wh = s_wh + warp * KWAY;
+  for (unsigned i = tid; i < NWARP * KWAY; i += NT) s_wh[i] = 0;
+  __syncthreads();
+#pragma unroll 2
+  for (int j = 0; j < CPT; ++j) {
+    const unsigned c = tid + j * NT;
+    const uint4 q = c < nwc ? sw[c] : make_uint4(0, 0, 0, 0);
+    const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
+#pragma unroll
+    for (unsigned v = 0; v < V; ++v) {
+      const unsigned off = 16 * c + v * KB;
+      const bool valid = full || (off >= lo && off < hi);
+      C k = key_at<KB>(q, v);
+      if (RAW) k = encode<KB>(k, a.codec);
+      const unsigned bk = valid ? bucket_of(k, split) : KWAY;
+      const unsigned peers = __match_any_sync(FULL, bk);
+      if (valid && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&wh[bk], (unsigned)__popc(peers));
+    }
+  }
+  __syncthreads();
+  if (!scatter) {
+    if (tid < KWAY) {
+      unsigned tot = 0;
+#pragma unroll
+      for (int w = 0; w < NWARP; ++w) tot += s_wh[w * KWAY + tid];
+      if (tot) atomicAdd(&kw.count[tid], (unsigned long long)tot);
+    }
+    return;
+  }
+  if (tid < KWAY) {
+    unsigned run = 0;
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) {
+      const unsigned x = s_wh[w * KWAY + tid];
+      s_wh[w * KWAY + tid] = run;
+      run += x;
+    }
+    unsigned long long base = run ? atomicAdd(&kw.cursor[tid], (unsigned long long)run) : 0ull;
+    if (run && base + run > __ldcg(&kw.start[tid + 1])) {   // guard: stay inside the bucket
+      guard_failed(a, GUARD_BUCKET);
+      base = ~0ull;
+    }
+    s_base[tid] = base;
+  }
+  __syncthreads();
+#pragma unroll 2
+  for (int j = 0; j < CPT; ++j) {
+    const unsigned c = tid + j * NT;
+    const uint4 q = c < nwc ? sw[c] : make_uint4(0, 0, 0, 0);
+    const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
+#pragma unroll
+    for (unsigned v = 0; v < V; ++v) {
+      const unsigned off = 16 * c + v * KB;
+      const bool valid = full || (off >= lo && off < hi);
+      C k = key_at<KB>(q, v);
+      if (RAW) k = encode<KB>(k, a.codec);
+      const unsigned bk = valid ? bucket_of(k, split) : KWAY;
+      const unsigned peers = __match_any_sync(FULL, bk);
+      if (valid && s_base[bk] != ~0ull) dst[s_base[bk] + wh[bk] + __popc(peers & ltm)] = to_mem<KB>(k);
+      __syncwarp();
+      if (valid && lane == (unsigned)(__ffs(peers) - 1)) wh[bk] += __popc(peers);
+      __syncwarp();
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Kernels.
 // ---------------------------------------------------------------------------
@@ -428,7 +693,8 @@ __global__ void k_prep(SortArgs a) {
 // Roots of the recursion: one range per segment (or the whole array).
 template <int KB> __global__ void __launch_bounds__(NT) k_seed(SortArgs a) {
   __shared__ RangeScratch rs;
-  __shared__ __align__(16) unsigned char scratch[SAMPLE * sizeof(typename KT<KB>::Code) + 64 * 8];
+  __shared__ __align__(16) unsigned char scratch[KWAY_SAMPLE * sizeof(typename KT<KB>::Code) + 1024 +
+                                                 KWAY * sizeof(typename KT<KB>::Code)];
   for (unsigned long long sg = blockIdx.x; sg < a.num_segments; sg += gridDim.x) {
     uint64_t b = 0, e = a.n_total;
     if (a.offsets) {
@@ -458,8 +724,19 @@ template <int KB> __global__ void __launch_bounds__(NT) k_seed(SortArgs a) {
       emit_fallback(a, b, m, SEG_RAW, rs);
     } else {
       if (threadIdx.x == 0) atomicAdd(&a.hdr->remaining, m);
-      const auto p = sample_pivot<KB>(a.keys, b, m, true, a.codec, range_seed(a.seed, b, 0), scratch);
-      make_segment<KB>(a, b, e, 0, SEG_RAW, p, limit, rs);
+      using C = typename KT<KB>::Code;
+      bool done = false;
+      if (a.kw && m >= KWAY_MIN) {
+        C *split = (C *)(scratch + KWAY_SAMPLE * sizeof(C) + 1024);
+        if (sample_splitters<KB>(a.keys, b, m, true, a.codec, range_seed(a.seed, b, 0), scratch, split)) {
+          make_kway_segment<KB>(a, b, e, 0, SEG_RAW, limit, split, rs);
+          done = true;
+        }
+      }
+      if (!done) {
+        const auto p = sample_pivot<KB>(a.keys, b, m, true, a.codec, range_seed(a.seed, b, 0), scratch);
+        make_segment<KB>(a, b, e, 0, SEG_RAW, p, limit, rs);
+      }
     }
     __syncthreads();
   }
@@ -477,6 +754,16 @@ __device__ __forceinline__ void load_desc(const SortArgs &a, unsigned long long 
   for (int k = 0; k < 8; ++k) sw[k] = w[k];
 }
 
+// Loads the splitters of K-way record `kid` (through L2) into shared memory.
+template <int KB>
+__device__ __forceinline__ void load_splitters(const SortArgs &a, unsigned long long kid,
+                                               typename KT<KB>::Code *split) {
+  const KwayDesc &kw = a.kw[kid];
+#pragma unroll
+  for (unsigned j = 0; j < KWAY - 1; ++j)
+    split[j] = code_of<KB>(__ldcg(&kw.split_lo[j]), KB == 16 ? __ldcg(&kw.split_hi[j]) : 0ull);
+}
+
 // Starts the TMA bulk copy of the tile's 16-byte-aligned window into `buf`.
 // The window may include up to 15 bytes on each side that belong to
 // neighbouring ranges; they are never used (and never cross a page).
@@ -484,11 +771,16 @@ template <int KB>
 __device__ __forceinline__ void issue_tile(const SortArgs &a, unsigned long long item, const SegDesc &seg,
                                            unsigned char *buf, uint64_t *bar) {
   const unsigned T = a.tile_keys;
-  const unsigned i = (unsigned)(item & 0xFFFFFFFFu);
+  const unsigned i = (unsigned)(item & 0x7FFFFFFFu);
   const uint64_t b = seg.begin, e = seg.end;
   const bool par = seg.flags & SEG_PARITY;
   const unsigned char *src = (const unsigned char *)(par ? a.alt : a.keys);
   const uint64_t t0 = b + (uint64_t)i * T;
+  if (t0 >= e || e > a.n_total) {   // guard: never copy outside the array
+    guard_failed(a, GUARD_TILE);
+    mbar_arrive_expect_tx(bar, 0);
+    return;
+  }
   const unsigned cnt = (unsigned)min((uint64_t)T, e - t0);
   const uintptr_t g0 = (uintptr_t)(src + t0 * KB), g1 = g0 + (uintptr_t)cnt * KB;
   const uintptr_t w0 = g0 & ~(uintptr_t)15, w1 = (g1 + 15) & ~(uintptr_t)15;
@@ -513,12 +805,15 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
   __shared__ uint64_t s_bar;
   __shared__ SegDesc s_seg, s_fseg;
   __shared__ unsigned long long s_item, s_ticket;
-  __shared__ unsigned s_fsid;
-  __shared__ int s_go, s_fin;
+  __shared__ unsigned s_fsid, s_fphase;
+  __shared__ int s_go, s_go2, s_fin;
   __shared__ unsigned s_wL[NWARP], s_wV[NWARP], s_bL[NWARP], s_bR[NWARP];
   __shared__ unsigned long long s_cur;
   __shared__ RangeScratch rs;
-  __shared__ __align__(16) unsigned char s_sample[SAMPLE * sizeof(C) + 64 * 8];
+  __shared__ __align__(16) unsigned char s_sample[KWAY_SAMPLE * sizeof(C) + 1024 + KWAY * sizeof(C)];
+  __shared__ C s_split[KWAY];
+  __shared__ unsigned s_wh[NWARP * KWAY];
+  __shared__ unsigned long long s_base[KWAY];
 
   const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
@@ -530,7 +825,7 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
   // Thread 0 state: the range whose descriptor is in s_seg, and the
   // completion count of the previous tile, read one claim later so that the
   // two round trips overlap.
-  unsigned seg_in_smem = ~0u, pend_sid = ~0u, pend_nt = 0;
+  unsigned seg_in_smem = ~0u, pend_sid = ~0u, pend_nt = 0, pend_phase = 0;
   uint32_t pend_prev = 0;
 
   for (;;) {
@@ -544,6 +839,7 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
         if (fin) {
           fence_acquire();
           s_fsid = pend_sid;
+          s_fphase = pend_phase;
           load_desc(a, (unsigned long long)pend_sid << 32, s_fseg);
         }
         pend_sid = ~0u;
@@ -554,6 +850,7 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
         const unsigned sid = (unsigned)((item >> 32) & 0x7FFFFFFFu);
         if (sid != seg_in_smem) {
           load_desc(a, item, s_seg);
+          if (s_seg.flags & SEG_KWAY) load_splitters<KB>(a, s_seg.piv_lo, s_split);
           seg_in_smem = sid;
         }
         issue_tile<KB>(a, item, s_seg, smem, &s_bar);
@@ -563,10 +860,16 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
     }
     __syncthreads();
     // the previous tile finished its range: the rest of Algorithm 1 for it
-    if (s_fin) finish_range<KB>(a, s_fseg, s_fsid, s_sample, rs);
+    if (s_fin) {
+      if (!(s_fseg.flags & SEG_KWAY)) finish_range<KB>(a, s_fseg, s_fsid, s_sample, rs);
+      else if (!s_fphase) finish_kway_count(a, s_fseg, s_fsid, rs);
+      else finish_kway_scatter<KB>(a, s_fseg, s_fsid, s_sample, rs);
+    }
     if (!s_go) {
       // the claimed item is not published yet (it may come from the range
-      // just finished above): wait for it
+      // just finished above): wait for it. The outcome goes to s_go2, not
+      // s_go: other warps may still be reading s_go for the test above, and
+      // a warp that saw it change would skip this block's barrier.
       if (tid == 0) {
         unsigned long long item = 0;
         const int go = wait_ticket(a, s_ticket, item);
@@ -575,14 +878,15 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
           const unsigned sid = (unsigned)((item >> 32) & 0x7FFFFFFFu);
           if (sid != seg_in_smem) {
             load_desc(a, item, s_seg);
+            if (s_seg.flags & SEG_KWAY) load_splitters<KB>(a, s_seg.piv_lo, s_split);
             seg_in_smem = sid;
           }
           issue_tile<KB>(a, item, s_seg, smem, &s_bar);
         }
-        s_go = go;
+        s_go2 = go;
       }
       __syncthreads();
-      if (!s_go) break;
+      if (!s_go2) break;
     }
     {
       unsigned it = 0;
@@ -597,7 +901,8 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
 
     const SegDesc &sg = s_seg;
     const unsigned sid = (unsigned)((s_item >> 32) & 0x7FFFFFFFu);
-    const unsigned i = (unsigned)(s_item & 0xFFFFFFFFu);
+    const unsigned i = (unsigned)(s_item & 0x7FFFFFFFu);
+    const bool phase1 = (s_item & ITEM_PHASE) != 0;
     const uint64_t b = sg.begin, e = sg.end;
     const bool par = sg.flags & SEG_PARITY, raw = sg.flags & SEG_RAW;
     const C piv = code_of<KB>(sg.piv_lo, sg.piv_hi);
@@ -610,6 +915,21 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
     const unsigned nwc = (unsigned)((((g1 + 15) & ~(uintptr_t)15) - w0) / 16);
     const unsigned lo = (unsigned)(g0 - w0), hi = (unsigned)(g1 - w0);
     const uint4 *sw = (const uint4 *)smem;
+
+    if (sg.flags & SEG_KWAY) {
+      KwayDesc &kw = a.kw[sg.piv_lo];
+      if (raw) kway_tile<KB, CPT, true>(a, sw, nwc, lo, hi, s_split, phase1, kw, dst, s_wh, s_base);
+      else kway_tile<KB, CPT, false>(a, sw, nwc, lo, hi, s_split, phase1, kw, dst, s_wh, s_base);
+      fence_proxy_async_smem();   // the next TMA copy reuses the window
+      __syncthreads();
+      if (tid == 0) {
+        pend_prev = atom_add_release(&a.segs[sid].tiles_done, 1u);
+        pend_sid = sid;
+        pend_nt = sg.ntiles;
+        pend_phase = phase1;
+      }
+      continue;
+    }
 
     // ---- pass 1: per-warp counts of left and valid keys
     unsigned nL = 0, nV = 0;
@@ -639,7 +959,12 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
       }
       if (lane == NWARP - 1) {
         const unsigned long long add = ((unsigned long long)(iV - iL) << 32) | iL;
-        s_cur = atomicAdd(&a.segs[sid].cursor, add);
+        unsigned long long cur = atomicAdd(&a.segs[sid].cursor, add);
+        if ((cur & 0xFFFFFFFFull) + (cur >> 32) + iV > e - b) {   // guard: slots inside the range
+          guard_failed(a, GUARD_BINARY);
+          cur = ~0ull;
+        }
+        s_cur = cur;
         if (anyLt) atomicOr(&a.segs[sid].has_lt, 1u);
       }
     }
@@ -647,7 +972,7 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
 
     // ---- pass 2: ballot ranks -> direct global stores. Left keys fill the
     // range from its start, right keys from its end.
-    {
+    if (s_cur != ~0ull) {
       const unsigned long long cur = s_cur;
       const unsigned tileL = s_bL[NWARP - 1] + s_wL[NWARP - 1];
       const unsigned tileR = cnt - tileL;
@@ -668,6 +993,7 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
       pend_prev = atom_add_release(&a.segs[sid].tiles_done, 1u);
       pend_sid = sid;
       pend_nt = sg.ntiles;
+      pend_phase = 0;
     }
   }
 }

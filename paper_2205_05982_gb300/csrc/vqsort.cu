@@ -54,6 +54,7 @@ int64_t g_spin_limit = 1 << 22;
 int64_t g_test_stall = 0;
 int64_t g_tile_bytes = 0;     // 0: 32 KiB partition tile windows
 int64_t g_leaf_threads = 0;   // 0: 16 keys per thread at the cutoff
+int64_t g_kway = 1;           // K-way levels for ranges of >= KWAY_MIN keys
 
 int tile_cpt() {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -71,8 +72,8 @@ unsigned leaf_cutoff_for(int kb) {
 // Workspace layout.
 // ---------------------------------------------------------------------------
 struct Layout {
-  size_t hdr, segs, items, lw, lb, fb, alt, total;
-  unsigned cap_q, cap_segs, cap_lw, cap_lb, cap_fb;
+  size_t hdr, segs, items, lw, lb, fb, kw, alt, total;
+  unsigned cap_q, cap_segs, cap_lw, cap_lb, cap_fb, cap_kw;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -87,7 +88,9 @@ Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_lim
   const uint64_t per_level = n / (C + 1ull) + 1;
   Layout L{};
   const uint64_t cap_segs = (levels + 1) * per_level + 16;
-  const uint64_t cap_q = (levels + 1) * ((n + T - 1) / T + per_level) + 16;
+  // a K-way range runs its tiles twice (counting pass, scatter pass)
+  const uint64_t cap_q = (levels + 1) * (2 * ((n + T - 1) / T) + per_level) + 16;
+  const uint64_t cap_kw = (levels + 1) * (n / KWAY_MIN + 1) + S + 16;
   const uint64_t cap_lw = 2 * cap_segs + S + 16;
   const uint64_t cap_lb = n / 512 + n / C + 2 * cap_segs + S + 16;
   const uint64_t cap_fb = n / (C + 1ull) + S + 16;
@@ -96,6 +99,7 @@ Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_lim
   L.cap_lw = (unsigned)cap_lw;
   L.cap_lb = (unsigned)cap_lb;
   L.cap_fb = (unsigned)cap_fb;
+  L.cap_kw = (unsigned)cap_kw;
   size_t off = 0;
   L.hdr = off; off = align256(off + sizeof(Header));
   L.segs = off; off = align256(off + cap_segs * sizeof(SegDesc));
@@ -103,6 +107,7 @@ Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_lim
   L.lw = off; off = align256(off + cap_lw * sizeof(LeafEntry));
   L.lb = off; off = align256(off + cap_lb * sizeof(LeafEntry));
   L.fb = off; off = align256(off + cap_fb * sizeof(LeafEntry));
+  L.kw = off; off = align256(off + cap_kw * sizeof(KwayDesc));
   L.alt = off;
   if (with_alt) off = align256(off + n * (uint64_t)kb);
   L.total = off;
@@ -236,7 +241,7 @@ struct Job {
 vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   const int kb = key_bytes(j.dt);
   const unsigned C = leaf_cutoff_for(kb);
-  int64_t depth_limit, seed, spin, stall, leaf_threads;
+  int64_t depth_limit, seed, spin, stall, leaf_threads, kway;
   const int cpt = j.mode == MODE_SORT ? tile_cpt() : PART_CPT;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -245,6 +250,7 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
     spin = g_spin_limit;
     stall = g_test_stall;
     leaf_threads = g_leaf_threads;
+    kway = g_kway;
   }
   const bool with_alt = j.mode == MODE_SORT;
   const Layout L = make_layout(kb, j.n, j.num_segments, C, depth_limit, with_alt, cpt);
@@ -260,6 +266,8 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   a.leaf_warp = (LeafEntry *)(w + L.lw);
   a.leaf_block = (LeafEntry *)(w + L.lb);
   a.fb = (LeafEntry *)(w + L.fb);
+  a.kw = (kway && j.mode == MODE_SORT) ? (KwayDesc *)(w + L.kw) : nullptr;
+  a.cap_kw = L.cap_kw;
   a.offsets = (const unsigned long long *)j.offsets;
   a.n_total = j.n;
   a.num_segments = j.num_segments;
@@ -479,6 +487,9 @@ vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out) {
   out->fallback_ranges = h.fallback_ranges;
   out->fallback_keys = h.fallback_keys;
   out->max_depth = h.max_depth;
+  out->keys_counted = h.keys_counted;
+  out->kway_ranges = h.kway_ranges;
+  out->guard = h.guard;
   out->device_status = h.error;
   return VQ_OK;
 }
@@ -522,6 +533,7 @@ vq_status vqsort_set_option(vq_option opt, int64_t value) {
       if (value != 0 && value != 256 && value != 512 && value != 1024) return VQ_ERR_INVALID;
       g_leaf_threads = value;
       return VQ_OK;
+    case VQ_OPT_KWAY: g_kway = value ? 1 : 0; return VQ_OK;
   }
   return VQ_ERR_INVALID;
 }
@@ -536,6 +548,7 @@ int64_t vqsort_get_option(vq_option opt) {
     case VQ_OPT_TEST_STALL: return g_test_stall;
     case VQ_OPT_TILE_BYTES: return g_tile_bytes;
     case VQ_OPT_LEAF_THREADS: return g_leaf_threads;
+    case VQ_OPT_KWAY: return g_kway;
   }
   return -1;
 }

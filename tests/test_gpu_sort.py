@@ -26,6 +26,7 @@ def check_sort(vq, oracle_mod, dtype, a, ascending):
     vq.sort_(t, dtype, descending=not ascending)
     got = to_host(t, dtype, a)
     assert vq.last_device_status() == 0
+    assert vq.stats()["guard"] == 0           # no range-bound guard fired
     if not same_bits(got, want):
         i, cnt = first_mismatch(got, want)
         pytest.fail(f"{dtype} n={len(a)} asc={ascending}: {cnt} mismatches, first at {i}")
@@ -233,7 +234,43 @@ def test_stats_are_consistent(vq):
     vq.sort_(t, "u64")
     st = vq.stats()
     assert st["device_status"] == 0
+    assert st["guard"] == 0
     assert st["leaf_keys"] + st["equal_keys"] + st["fallback_keys"] == n
     assert st["keys_partitioned"] >= n            # at least the root level
     assert st["max_depth"] <= 2 * 23 + 4
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("kway", (0, 1))
+@pytest.mark.parametrize("dtype", ("u16", "i32", "f32", "u64", "f64", "u128", "kv64"))
+@pytest.mark.parametrize("dist", ("uniform", "distinct16", "equal", "sorted", "organpipe"))
+def test_kway_levels_on_and_off(vq, oracle_mod, kway, dtype, dist):
+    """Ranges of >= 2^18 keys are split 16 ways (counting + scatter pass) when
+    the option is on; the output must not change."""
+    vq.set_option("kway", kway)
+    try:
+        a = make(dtype, 1_500_007, dist, seed=13)
+        check_sort(vq, oracle_mod, dtype, a, True)
+        st = vq.stats()
+        if kway and dist in ("uniform", "sorted", "organpipe"):
+            assert st["kway_ranges"] >= 1
+        if not kway:
+            assert st["kway_ranges"] == 0
+        check_sort(vq, oracle_mod, dtype, a, False)
+    finally:
+        vq.set_option("kway", 1)
+
+
+@pytest.mark.parametrize("n", (30_000_000, 10_000_003))
+def test_kway_mid_sizes_with_workspace(vq, oracle_mod, n):
+    """Sizes whose second level is still K-way but whose third is two-way,
+    through the caller-owned workspace form (as the benchmark calls it)."""
+    a = inputs.make("u64", n, "uniform", seed=n % 97)
+    want = oracle_mod.sort(a, "u64", True)
+    ws = vq.alloc_workspace("u64", n)
+    for _ in range(3):
+        t = to_dev(a, "u64")
+        vq.sort_ws_(t, ws, "u64")
+        assert vq.last_device_status(ws) == 0, vq.stats(ws)
+        assert vq.stats(ws)["guard"] == 0
+        assert same_bits(to_host(t, "u64", a), want)
