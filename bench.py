@@ -74,6 +74,13 @@ def dist_env():
     return rank, world, local
 
 
+def partition_bytes(kb: int, st: dict) -> int:
+    """Algorithmic bytes of one partition launch: every partitioned key is
+    read and written once (two-way and K-way scatter passes), and K-way
+    ranges read their keys once more in the counting pass."""
+    return kb * (2 * st["keys_partitioned"] + st["keys_counted"])
+
+
 def hbm_peak():
     try:
         with open(PEAKS_FILE) as f:
@@ -250,7 +257,7 @@ def extra_dtypes(vq, torch, peak, n):
         kb = inputs.KEY_BYTES[dt]
         part = prof.get("partition", {"ms": float("nan"), "launches": 1})
         part_ms = part["ms"] / max(1, part["launches"])
-        pb = 2 * kb * st["keys_partitioned"]
+        pb = partition_bytes(kb, st)
         out[dt] = {"gkeys_per_s": n / (ms * 1e-3) / 1e9, "ms": ms,
                    "partition_frac": pb / (part_ms * 1e-3) / 1e9 / peak,
                    "sort_frac": (pb + 2 * kb * n) / (ms * 1e-3) / 1e9 / peak,
@@ -399,7 +406,7 @@ def run_gpu(args):
     # roofline of the dominant kernel (the persistent partition kernel)
     part = prof.get("partition", {"ms": float("nan"), "launches": 1})
     part_ms = part["ms"] / max(1, part["launches"])
-    part_bytes = 2 * kb * st["keys_partitioned"]
+    part_bytes = partition_bytes(kb, st)
     peak, peak_kind = hbm_peak()
     achieved = part_bytes / (part_ms * 1e-3) / 1e9
     traffic = None
@@ -447,7 +454,8 @@ def run_gpu(args):
         "sort_roofline": {"bytes_per_step": sort_bytes,
                           "achieved_gbs": sort_bytes / (ms_step * 1e-3) / 1e9,
                           "frac": sort_bytes / (ms_step * 1e-3) / 1e9 / peak,
-                          "levels_run_keys": st["keys_partitioned"], "max_depth": st["max_depth"],
+                          "levels_run_keys": st["keys_partitioned"], "keys_counted": st["keys_counted"],
+                          "kway_ranges": st["kway_ranges"], "max_depth": st["max_depth"],
                           "leaf_ms_per_step": leaf_ms},
         "kernels": kernels,
         "kernel_hash": kernel_hash(),

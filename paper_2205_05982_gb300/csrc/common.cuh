@@ -204,6 +204,9 @@ __device__ __forceinline__ uint32_t atom_add_release(unsigned int *p, uint32_t v
   return old;
 }
 __device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// The same fence used on the release side: followed by relaxed stores it
+// publishes everything ordered before it (one fence for many stores).
+__device__ __forceinline__ void fence_release() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -296,7 +299,7 @@ enum : unsigned int {
   SEG_PARITY = 1u,   // keys live in the alternate buffer (else the user buffer)
   SEG_RAW = 2u,      // keys are still in input form (root ranges)
   SEG_EXCL = 4u,     // pivot is one below a repeated maximum: right side all equal
-  SEG_KWAY = 16u,    // split KWAY ways by the splitters of K-way record piv_lo
+  SEG_KWAY = 16u,    // split 2^piv_hi ways by the splitters of K-way record piv_lo
   SEG_NOKWAY = 32u,  // a K-way split made no progress here: split in two
 };
 
@@ -309,21 +312,43 @@ struct LeafEntry {
 enum : unsigned int { LEAF_COPY = 8u };   // all keys equal: decode and copy only
 
 // Work-queue item: bit 63 valid, bits 32..62 segment id, bit 31 phase (K-way
-// ranges: 0 = counting pass, 1 = scatter pass), bits 0..30 tile.
+// ranges: 0 = counting pass, 1 = scatter pass), bit 30 setup (start child
+// `index` of the segment: sample it and publish its tiles), bit 29 (setup
+// items) the child is split in two, bits 0..28 the tile or child index.
 constexpr unsigned long long ITEM_VALID = 1ull << 63;
 constexpr unsigned long long ITEM_PHASE = 1ull << 31;
+constexpr unsigned long long ITEM_SETUP = 1ull << 30;
+constexpr unsigned long long ITEM_NOKWAY = 1ull << 29;
+constexpr unsigned long long ITEM_INDEX = (1ull << 29) - 1;
 
-// K-way levels (samplesort-style multi-pivot partition for large ranges).
-constexpr unsigned KWAY = 16;              // buckets per K-way level
-constexpr unsigned KWAY_SAMPLE = 512;      // keys in the splitter sample
-constexpr unsigned long long KWAY_MIN = 1ull << 18;   // smallest range split K ways
+// K-way levels (multi-pivot partition of large ranges): 2^4 .. 2^8 buckets.
+constexpr unsigned KW_MIN_BITS = 4;
+constexpr unsigned KW_MAX_BITS = 8;
+constexpr unsigned KW_MAX = 1u << KW_MAX_BITS;
+// Tile i of a K-way range updates counter stripe i % KW_STRIPES, so the
+// atomics of one large range spread over KW_STRIPES x 8 cache lines.
+constexpr unsigned KW_STRIPES = 16;
 
-// Splitters and per-bucket counters of one K-way range.
+// Buckets are looked up by KW_TABLE_BITS key bits after the prefix that the
+// first and last splitter share.
+constexpr unsigned KW_TABLE_BITS = 10;
+constexpr unsigned KW_TABLE = 1u << KW_TABLE_BITS;
+
+// Splitters and per-bucket counters of one K-way range (K = 2^kbits buckets,
+// kbits kept in the range descriptor's piv_hi).
 struct KwayDesc {
-  unsigned long long split_lo[KWAY], split_hi[KWAY];   // KWAY-1 splitter codes (ascending)
-  unsigned long long count[KWAY];    // counting pass: keys per bucket (atomic)
-  unsigned long long cursor[KWAY];   // scatter pass: next free slot per bucket (atomic)
-  unsigned long long start[KWAY + 1];// bucket bounds (key indices), set between the passes
+  // counting pass: keys of stripe s in bucket b (atomic); then, for the
+  // scatter pass, the next free slot of stripe s in bucket b, relative to the
+  // range start (atomic). Ranges are shorter than 2^32 keys.
+  unsigned int cnt[KW_STRIPES][KW_MAX];
+  unsigned long long start[KW_MAX + 1];  // bucket bounds (key indices), set between the passes
+  unsigned long long split_lo[KW_MAX];   // splitters 1..K-1, ascending
+  unsigned long long split_hi[KW_MAX];   // (high words: 16-byte keys only)
+  // per value p of the table bits: (number of splitters whose table bits
+  // are below p) | (number equal to p) << 8
+  unsigned short table[KW_TABLE];
+  unsigned int shift;                    // leading bits shared by splitters 1 and K-1
+  unsigned int pad;
 };
 
 // Warp leaves handle ranges up to this many keys (32 lanes x 16 keys).
@@ -352,6 +377,9 @@ struct SortArgs {
   unsigned long long seed;
   unsigned int cap_q, cap_segs, cap_leaf_warp, cap_leaf_block, cap_fb, cap_kw;
   unsigned int tile_keys;              // keys per partition tile
+  unsigned int kw_tile_keys;           // keys per K-way tile
+  unsigned int kw_min_keys;            // smallest range split K ways
+  unsigned int kw_target;              // aimed-for keys per K-way bucket
   unsigned int tile_cpt;               // 16-byte chunks per thread of the partition tile window
   unsigned int leaf_threads;           // threads of a block-leaf CTA (0: 16 keys per thread)
   unsigned int leaf_cutoff;            // ranges <= this go to the leaf kernels

@@ -21,6 +21,13 @@ __host__ __device__ constexpr unsigned part_tile_keys(int kb, int cpt = PART_CPT
   return (unsigned)((part_window(cpt) - 16) / kb);
 }
 
+// K-way tiles: keys in the first half of the window, the second half stages
+// them in bucket order; at most 16 keys per thread.
+__host__ __device__ constexpr int kw_cpt(int kb, int cpt) { return cpt / 2 < kb ? cpt / 2 : kb; }
+__host__ __device__ constexpr unsigned kw_tile_keys(int kb, int cpt = PART_CPT) {
+  return (unsigned)((PART_NT * kw_cpt(kb, cpt) * 16 - 16) / kb);
+}
+
 constexpr int LEAF_NT = 1024;       // threads of the block leaf kernel
 constexpr int FB_NT = 256;          // threads of the merge fallback kernel
 constexpr int FB_R = 8;             // keys per thread in its chunk sort

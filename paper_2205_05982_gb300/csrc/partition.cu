@@ -127,6 +127,16 @@ __device__ typename KT<KB>::Code sample_pivot(const void *buf, uint64_t b, uint6
 // Range bookkeeping (whole block).
 // ---------------------------------------------------------------------------
 
+// Publishes `count` queue items from slot q0 on: item k = bits | k. Each
+// thread fences once (ordering the range's descriptor, written before the
+// caller's barrier) and then stores its items relaxed.
+__device__ __forceinline__ void publish_items(const SortArgs &a, unsigned long long q0, unsigned count,
+                                              unsigned long long bits) {
+  if (threadIdx.x >= count) return;
+  fence_release();
+  for (unsigned k = threadIdx.x; k < count; k += blockDim.x) st_relaxed(&a.items[q0 + k], bits | k);
+}
+
 // Creates a range to partition and publishes its tiles as queue items.
 template <int KB>
 __device__ void make_segment(const SortArgs &a, uint64_t b, uint64_t e, unsigned depth, unsigned flags,
@@ -161,13 +171,9 @@ __device__ void make_segment(const SortArgs &a, uint64_t b, uint64_t e, unsigned
     rs.ok = ok;
   }
   __syncthreads();
-  if (rs.ok) {
-    // the descriptor (written by thread 0, ordered by the barrier above) is
-    // published with each item's release store
-    const unsigned long long q0 = rs.q0, sid = rs.sid;
-    for (unsigned k = threadIdx.x; k < nt; k += blockDim.x)
-      st_release(&a.items[q0 + k], ITEM_VALID | (sid << 32) | k);
-  }
+  // the descriptor (written by thread 0, ordered by the barrier above) is
+  // published with the items
+  if (rs.ok) publish_items(a, rs.q0, nt, ITEM_VALID | (rs.sid << 32));
   __syncthreads();
 }
 
@@ -229,26 +235,102 @@ __device__ void emit_fallback(const SortArgs &a, uint64_t b, uint64_t m, unsigne
 }
 
 // ---------------------------------------------------------------------------
-// K-way ranges (the paper's K > 2 partition, Sec. 4.2, taken further on the
-// GPU): KWAY-1 splitters from a 512-key sample; a counting pass over the
-// range's tiles builds the bucket histogram, a scatter pass writes every key
-// to its bucket. Keys equal to a splitter go to the lower bucket (the "<="
-// rule of the binary partition).
+// K-way ranges. The paper tried a K > 2 partition only as a prototype (Sec.
+// 4.2); on the GPU a split into K = 2^kbits buckets (16..256) costs one
+// counting pass and one scatter pass, where two-way levels would need kbits
+// passes. Splitters come from a sorted random sample; bucket j holds the keys
+// above splitter j and at most splitter j+1 (keys equal to a splitter take
+// the lower bucket, the "<=" rule of the two-way partition). A key's bucket
+// is found through a table indexed by the KW_TABLE_BITS code bits that follow
+// the prefix shared by the first and the last splitter: the table gives the
+// splitters certainly below the key and the few (usually none or one) that
+// share its table bits, which are then compared.
 // ---------------------------------------------------------------------------
 
-// Samples KWAY_SAMPLE keys of [b, b+m) (64-byte chunks drawn as in
-// sample_pivot), sorts them with the block network and writes the splitters
-// (ranks 32j-1, j = 1..KWAY-1) to `split` (shared). Returns false when the
-// sample holds a single value (the binary path handles such ranges).
-template <int KB>
-__device__ bool sample_splitters(const void *buf, uint64_t b, uint64_t m, bool raw, Codec cd, uint64_t seed,
-                                 void *scratch, typename KT<KB>::Code *split) {
+// Keys per thread of the splitter sample: as many as the scratch holds.
+template <int KB, int CPT> __host__ __device__ constexpr unsigned kw_sample_r() {
+  return KB == 16 ? (CPT >= 8 ? 4u : 2u) : (CPT >= 8 ? 8u : 4u);
+}
+template <int KB, unsigned R> __host__ __device__ constexpr unsigned kw_scratch_bytes() {
+  return R * NT * (unsigned)sizeof(typename KT<KB>::Code) + R * NT / (64 / KB) * 8u;
+}
+
+// Leading bits shared by two codes (the code width when they are equal).
+__device__ __forceinline__ unsigned common_prefix(uint32_t x, uint32_t y) { return x == y ? 32u : __clz(x ^ y); }
+__device__ __forceinline__ unsigned common_prefix(uint64_t x, uint64_t y) { return x == y ? 64u : __clzll(x ^ y); }
+__device__ __forceinline__ unsigned common_prefix(const U128 &x, const U128 &y) {
+  return x.hi != y.hi ? (unsigned)__clzll(x.hi ^ y.hi) : x.lo != y.lo ? 64u + __clzll(x.lo ^ y.lo) : 128u;
+}
+
+// The KW_TABLE_BITS bits of code k that follow its first `sh` bits (zeros
+// past the end of the code); sh is below the code width.
+__device__ __forceinline__ unsigned table_bits(uint32_t k, unsigned sh) {
+  return (k << (sh & 31)) >> (32 - KW_TABLE_BITS);
+}
+__device__ __forceinline__ unsigned table_bits(uint64_t k, unsigned sh) {
+  return (unsigned)((k << (sh & 63)) >> (64 - KW_TABLE_BITS));
+}
+__device__ __forceinline__ unsigned table_bits(const U128 &k, unsigned sh) {
+  const unsigned s = sh & 127;
+  const uint64_t top = s == 0 ? k.hi : s < 64 ? (k.hi << s) | (k.lo >> (64 - s)) : k.lo << (s - 64);
+  return (unsigned)(top >> (64 - KW_TABLE_BITS));
+}
+
+// Bucket of code k: the number of splitters strictly below it. split[1..K-1]
+// ascending, s1 = split[1], sk = split[K-1], sh = their shared prefix.
+template <class C>
+__device__ __forceinline__ unsigned classify(const C &k, const C *split, const unsigned short *table,
+                                             const C &s1, const C &sk, unsigned sh, unsigned K) {
+  if (!lt(s1, k)) return 0;
+  if (lt(sk, k)) return K - 1;
+  // s1 < k <= sk: k shares the prefix, so every splitter with smaller
+  // table bits is below k and every one with larger bits above it
+  const unsigned e = table[table_bits(k, sh)];
+  unsigned b = e & 255u, n = e >> 8;
+  while (n) {   // count the ones with equal bits that are below k
+    const unsigned h = n >> 1;
+    if (lt(split[b + h + 1], k)) {
+      b += h + 1;
+      n -= h + 1;
+    } else {
+      n = h;
+    }
+  }
+  return b;
+}
+
+// The bucket lookup of one K-way range, staged in shared memory.
+template <class C> struct KwLookup {
+  const C *split;
+  const unsigned short *table;
+  C s1, sk;
+  unsigned sh, K;
+  __device__ __forceinline__ unsigned operator()(const C &k) const {
+    return classify(k, split, table, s1, sk, sh, K);
+  }
+};
+
+// Buckets for a range of m keys: about kw_target keys each, 16..256 of them.
+__device__ __forceinline__ unsigned kway_bits(const SortArgs &a, uint64_t m) {
+  unsigned bits = KW_MIN_BITS;
+  while (bits < KW_MAX_BITS && ((uint64_t)a.kw_target << bits) < m) ++bits;
+  return bits;
+}
+
+// Samples R*NT keys of [b, b+m) (64-byte chunks drawn as in sample_pivot),
+// sorts them with the block network and writes splitter i = sample rank
+// i*S/K - 1 (i = 1..K-1) and the lookup table to `kw`. Returns false,
+// writing nothing, when every sampled code is the same (such ranges are
+// split in two).
+template <int KB, unsigned R>
+__device__ bool build_splitters(const void *buf, uint64_t b, uint64_t m, bool raw, Codec cd, uint64_t seed,
+                                unsigned kbits, KwayDesc &kw, void *scratch) {
   using C = typename KT<KB>::Code;
-  constexpr unsigned kc = 64 / KB, ns = KWAY_SAMPLE / kc;
-  constexpr unsigned R = KWAY_SAMPLE / NT;   // 2 keys per thread
-  static_assert(R * NT == KWAY_SAMPLE, "sample layout");
+  constexpr unsigned S = R * NT, kc = 64 / KB, ns = S / kc;
+  static_assert(S >= KW_MAX, "at least one sample per bucket");
+  constexpr unsigned WIDTH = 8 * sizeof(C);
   C *sx = (C *)scratch;
-  unsigned long long *s_chunk = (unsigned long long *)(sx + KWAY_SAMPLE);
+  unsigned long long *s_chunk = (unsigned long long *)(sx + S);
   __shared__ int s_same;
   const uintptr_t addr = (uintptr_t)buf + b * KB;
   const uint64_t off = ((64 - (addr & 63)) & 63) / KB;
@@ -263,41 +345,79 @@ __device__ bool sample_splitters(const void *buf, uint64_t b, uint64_t m, bool r
 #pragma unroll
   for (unsigned r = 0; r < R; ++r) {
     const unsigned i = threadIdx.x + r * NT;
-    C c = load_cg<KB>(buf, b + off + s_chunk[i / kc] * kc + i % kc);
+    const C c = load_cg<KB>(buf, b + off + s_chunk[i / kc] * kc + i % kc);
     k[r] = raw ? encode<KB>(c, cd) : c;
   }
-  group_sort<C, R, NT>(k, threadIdx.x, sx);
-  // thread t holds sorted ranks 2t, 2t+1
-  if (threadIdx.x % 16 == 15 && threadIdx.x < NT - 1) split[threadIdx.x / 16] = k[1];
+  group_sort<C, R, NT>(k, threadIdx.x, sx);   // thread t: sample ranks R*t .. R*t+R-1
   if (threadIdx.x == 0) sx[0] = k[0];
   __syncthreads();
   if (threadIdx.x == NT - 1) s_same = eq(sx[0], k[R - 1]);
   __syncthreads();
-  const bool ok = !s_same;
+  const bool same = s_same;
+  if (same) return false;   // uniform across the block
+  const unsigned K = 1u << kbits, step = S >> kbits;
+  C *sp = sx;   // splitters 1..K-1
+#pragma unroll
+  for (unsigned r = 0; r < R; ++r) {
+    const unsigned rank1 = R * threadIdx.x + r + 1;
+    const unsigned i = rank1 / step;
+    if (rank1 % step == 0 && i < K) {
+      sp[i] = k[r];
+      uint64_t lo, hi;
+      code_words<KB>(k[r], lo, hi);
+      kw.split_lo[i] = lo;
+      kw.split_hi[i] = hi;
+    }
+  }
   __syncthreads();
-  return ok;
+  const unsigned sh = common_prefix(sp[1], sp[K - 1]);
+  if (threadIdx.x == 0) kw.shift = sh;
+  // table[p]: splitters (1..K-1, all sharing the prefix, so their table bits
+  // ascend with i) whose table bits are below p, and how many equal p
+  for (unsigned p = threadIdx.x; p < KW_TABLE; p += NT) {
+    unsigned below = 0, upto = 0;
+    if (sh < WIDTH) {
+      unsigned lo = 1, n = K - 1;   // first i with bits(sp[i]) >= p
+      while (n) {
+        const unsigned h = n >> 1;
+        if (table_bits(sp[lo + h], sh) < p) { lo += h + 1; n -= h + 1; } else n = h;
+      }
+      below = lo - 1;
+      unsigned lo2 = lo, n2 = K - lo;   // first i with bits(sp[i]) > p
+      while (n2) {
+        const unsigned h = n2 >> 1;
+        if (table_bits(sp[lo2 + h], sh) <= p) { lo2 += h + 1; n2 -= h + 1; } else n2 = h;
+      }
+      upto = lo2 - 1;
+    }
+    kw.table[p] = (unsigned short)(below | ((upto - below) << 8));
+  }
+  __syncthreads();
+  return true;
 }
 
-// Creates a K-way range with the splitters in `split` (shared) and publishes
-// its counting-pass tiles.
-template <int KB>
+// Creates a K-way range on record `kid` (splitters already written) and
+// publishes its counting-pass tiles.
 __device__ void make_kway_segment(const SortArgs &a, uint64_t b, uint64_t e, unsigned depth, unsigned flags,
-                                  unsigned depth_limit, const typename KT<KB>::Code *split, RangeScratch &rs) {
-  const unsigned T = a.tile_keys;
+                                  unsigned depth_limit, unsigned long long kid, unsigned kbits,
+                                  RangeScratch &rs) {
+  const unsigned T = a.kw_tile_keys;
   const uint64_t m = e - b;
   const unsigned nt = (unsigned)((m + T - 1) / T);
-  __shared__ unsigned long long s_kid;
+  KwayDesc &kw = a.kw[kid];
+  for (unsigned j = threadIdx.x; j < (1u << kbits); j += NT)
+#pragma unroll
+    for (unsigned st = 0; st < KW_STRIPES; ++st) kw.cnt[st][j] = 0;
   if (threadIdx.x == 0) {
     const unsigned long long sid = atomicAdd(&a.hdr->nseg, 1ull);
-    const unsigned long long kid = atomicAdd(&a.hdr->nkw, 1ull);
     const unsigned long long q0 = atomicAdd(&a.hdr->tail, (unsigned long long)nt);
-    const int ok = sid < a.cap_segs && kid < a.cap_kw && q0 + nt <= a.cap_q && sid < (1ull << 31);
+    const int ok = sid < a.cap_segs && q0 + nt <= a.cap_q && sid < (1ull << 31);
     if (ok) {
       SegDesc &d = a.segs[sid];
       d.begin = b;
       d.end = e;
       d.piv_lo = kid;
-      d.piv_hi = 0;
+      d.piv_hi = kbits;
       d.cursor = 0;
       d.depth = depth;
       d.flags = flags | SEG_KWAY;
@@ -311,35 +431,66 @@ __device__ void make_kway_segment(const SortArgs &a, uint64_t b, uint64_t e, uns
     rs.sid = sid;
     rs.q0 = q0;
     rs.ok = ok;
-    s_kid = kid;
   }
   __syncthreads();
-  if (rs.ok) {
-    KwayDesc &kw = a.kw[s_kid];
-    for (unsigned j = threadIdx.x; j < KWAY; j += blockDim.x) {
-      uint64_t lo = 0, hi = 0;
-      if (j < KWAY - 1) code_words<KB>(split[j], lo, hi);
-      kw.split_lo[j] = lo;
-      kw.split_hi[j] = hi;
-      kw.count[j] = 0;
-      kw.cursor[j] = 0;
-    }
-    __syncthreads();
-    const unsigned long long q0 = rs.q0, sid = rs.sid;
-    for (unsigned k = threadIdx.x; k < nt; k += blockDim.x)
-      st_release(&a.items[q0 + k], ITEM_VALID | (sid << 32) | k);
-  }
+  // the counters (zeroed above) and the descriptor are published with the items
+  if (rs.ok) publish_items(a, rs.q0, nt, ITEM_VALID | (rs.sid << 32));
   __syncthreads();
 }
 
-// A child of a partitioned range: leaf, fallback, or a new range to
-// partition (Algorithm 1: BaseCase for small sides, ChoosePivot + Recurse
-// otherwise; the depth bound of Sec. 2.2 before recursing). Returns the keys
-// handed to a leaf list or the fallback.
+// Starts partitioning [b, e) (more than a leaf, depth below its bound):
+// a K-way range when it is large enough and its sample has two values or
+// more, else a two-way range around a sampled pivot (Algorithm 1's
+// ChoosePivot). `scratch` holds kw_scratch_bytes<KB, R>() bytes.
+template <int KB, unsigned R>
+__device__ void start_range(const SortArgs &a, uint64_t b, uint64_t e, unsigned depth, unsigned flags,
+                            unsigned depth_limit, bool allow_kway, void *scratch, RangeScratch &rs) {
+  const uint64_t m = e - b;
+  const bool raw = flags & SEG_RAW;
+  const void *buf = (flags & SEG_PARITY) ? a.alt : a.keys;
+  const uint64_t seed = range_seed(a.seed, b, depth);
+  if (allow_kway && a.kw && m >= a.kw_min_keys) {
+    if (threadIdx.x == 0) {
+      const unsigned long long kid = atomicAdd(&a.hdr->nkw, 1ull);
+      rs.idx = kid < a.cap_kw ? kid : ~0ull;   // no record left: split in two
+    }
+    __syncthreads();
+    const unsigned long long kid = rs.idx;
+    __syncthreads();
+    if (kid != ~0ull) {
+      const unsigned kbits = kway_bits(a, m);
+      if (build_splitters<KB, R>(buf, b, m, raw, a.codec, seed, kbits, a.kw[kid], scratch)) {
+        make_kway_segment(a, b, e, depth, flags, depth_limit, kid, kbits, rs);
+        return;
+      }
+    }
+  }
+  const auto p = sample_pivot<KB>(buf, b, m, raw, a.codec, seed, scratch);
+  make_segment<KB>(a, b, e, depth, flags | (allow_kway ? 0u : SEG_NOKWAY), p, depth_limit, rs);
+}
+
+// Thread 0: queues the setup of child j of range psid (sampled later by
+// whichever block claims the item).
+__device__ void publish_setup(const SortArgs &a, unsigned psid, unsigned j, bool nokway) {
+  const unsigned long long q = atomicAdd(&a.hdr->tail, 1ull);
+  if (q >= a.cap_q) {
+    raise_error(a, ERR_INTERNAL);
+    return;
+  }
+  st_release(&a.items[q], ITEM_VALID | ((unsigned long long)psid << 32) | ITEM_SETUP |
+                              (nokway ? ITEM_NOKWAY : 0ull) | j);
+}
+
+// A child [b, e) of two-way range psid (j = 0 left, 1 right): leaf,
+// fallback, or a new range to partition (Algorithm 1: BaseCase for small
+// sides, ChoosePivot + Recurse otherwise; the depth bound of Sec. 2.2
+// before recursing). Children large enough for a K-way split are queued as
+// setup items, whose larger sample does not fit this block's free scratch.
+// Returns the keys handed to a leaf list or the fallback.
 template <int KB>
 __device__ uint64_t child_range(const SortArgs &a, uint64_t b, uint64_t e, unsigned depth, unsigned parity,
-                                unsigned depth_limit, void *scratch, RangeScratch &rs, bool allow_kway = true) {
-  using C = typename KT<KB>::Code;
+                                unsigned depth_limit, void *scratch, RangeScratch &rs, unsigned psid,
+                                unsigned j) {
   const uint64_t m = e - b;
   if (m == 0) return 0;
   if (m <= a.leaf_cutoff) {
@@ -350,80 +501,176 @@ __device__ uint64_t child_range(const SortArgs &a, uint64_t b, uint64_t e, unsig
     emit_fallback(a, b, m, parity, rs);
     return m;
   }
-  const void *buf = parity ? a.alt : a.keys;
-  const uint64_t seed = range_seed(a.seed, b, depth);
-  if (allow_kway && a.kw && m >= KWAY_MIN) {
-    C *split = (C *)((unsigned char *)scratch + KWAY_SAMPLE * sizeof(C) + 1024);
-    if (sample_splitters<KB>(buf, b, m, false, a.codec, seed, scratch, split)) {
-      make_kway_segment<KB>(a, b, e, depth, parity, depth_limit, split, rs);
-      return 0;
-    }
+  if (a.kw && m >= a.kw_min_keys) {
+    if (threadIdx.x == 0) publish_setup(a, psid, j, false);
+    return 0;
   }
-  const auto p = sample_pivot<KB>(buf, b, m, false, a.codec, seed, scratch);
-  make_segment<KB>(a, b, e, depth, parity | (allow_kway ? 0u : SEG_NOKWAY), p, depth_limit, rs);
+  const auto p = sample_pivot<KB>(parity ? a.alt : a.keys, b, m, false, a.codec, range_seed(a.seed, b, depth),
+                                  scratch);
+  make_segment<KB>(a, b, e, depth, parity, p, depth_limit, rs);
   return 0;
 }
 
+// Exclusive scan of one value per thread over the block; `total` gets the sum.
+__device__ unsigned long long block_excl_scan(unsigned long long x, unsigned long long *s_w,
+                                              unsigned long long &total) {
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= (unsigned)o) incl += y;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  unsigned long long pre = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < NWARP; ++w) {
+    const unsigned long long v = s_w[w];
+    if (w < (int)warp) pre += v;
+    tot += v;
+  }
+  __syncthreads();
+  total = tot;
+  return pre + incl - x;
+}
+
 // After the counting pass of a K-way range: bucket bounds from the counts,
-// then the scatter-pass tiles.
-__device__ void finish_kway_count(const SortArgs &a, const SegDesc &sd, unsigned sid, RangeScratch &rs) {
+// each stripe's write cursor at its share of the bucket, then the
+// scatter-pass tiles.
+__device__ void finish_kway_count(const SortArgs &a, const SegDesc &sd, unsigned sid, RangeScratch &rs,
+                                  unsigned long long *s_w) {
   KwayDesc &kw = a.kw[sd.piv_lo];
-  if (threadIdx.x == 0) {
-    unsigned long long pos = sd.begin;
-    for (unsigned j = 0; j < KWAY; ++j) {
-      kw.start[j] = pos;
-      kw.cursor[j] = pos;
-      pos += ld_relaxed(&kw.count[j]);
+  const unsigned K = 1u << sd.piv_hi;
+  const unsigned tid = threadIdx.x;
+  unsigned c[KW_STRIPES];
+  unsigned long long cnt = 0;
+#pragma unroll
+  for (unsigned st = 0; st < KW_STRIPES; ++st) {
+    c[st] = tid < K ? __ldcg(&kw.cnt[st][tid]) : 0u;
+    cnt += c[st];
+  }
+  unsigned long long total;
+  const unsigned long long excl = block_excl_scan(cnt, s_w, total);
+  if (tid < K) {
+    kw.start[tid] = sd.begin + excl;
+    unsigned run = (unsigned)excl;
+#pragma unroll
+    for (unsigned st = 0; st < KW_STRIPES; ++st) {
+      kw.cnt[st][tid] = run;
+      run += c[st];
     }
-    kw.start[KWAY] = pos;   // == sd.end
+  }
+  if (tid == 0) {
+    kw.start[K] = sd.begin + total;
+    if (sd.begin + total != sd.end) guard_failed(a, GUARD_BOUNDS);
     a.segs[sid].tiles_done = 0;
     atomicAdd(&a.hdr->keys_counted, sd.end - sd.begin);
     const unsigned long long q0 = atomicAdd(&a.hdr->tail, (unsigned long long)sd.ntiles);
     rs.q0 = q0;
-    rs.ok = q0 + sd.ntiles <= a.cap_q;
-    if (!rs.ok) raise_error(a, ERR_INTERNAL);
+    rs.ok = q0 + sd.ntiles <= a.cap_q && sd.begin + total == sd.end;
+    if (q0 + sd.ntiles > a.cap_q) raise_error(a, ERR_INTERNAL);
   }
   __syncthreads();
-  if (rs.ok) {
-    const unsigned long long q0 = rs.q0;
-    for (unsigned k = threadIdx.x; k < sd.ntiles; k += blockDim.x)
-      st_release(&a.items[q0 + k], ITEM_VALID | ((unsigned long long)sid << 32) | ITEM_PHASE | k);
-  }
+  if (rs.ok) publish_items(a, rs.q0, sd.ntiles, ITEM_VALID | ((unsigned long long)sid << 32) | ITEM_PHASE);
   __syncthreads();
 }
 
-// After the scatter pass of a K-way range: its KWAY buckets are the children.
-template <int KB>
-__device__ void finish_kway_scatter(const SortArgs &a, const SegDesc &sd, unsigned sid, void *scratch,
-                                    RangeScratch &rs) {
+// After the scatter pass of a K-way range: its buckets are the children, one
+// per thread. Leaves and fallback ranges are listed here; every larger child
+// becomes a setup item, so up to 256 children are sampled by as many blocks.
+__device__ void finish_kway_scatter(const SortArgs &a, const SegDesc &sd, unsigned sid,
+                                    unsigned long long *s_w) {
   if (a.test_stall && sid == 0) return;   // test hook: children never appear
   const KwayDesc &kw = a.kw[sd.piv_lo];
+  const unsigned K = 1u << sd.piv_hi;
+  const unsigned tid = threadIdx.x;
   const unsigned parity = (sd.flags & SEG_PARITY) ^ 1u;
   const unsigned d1 = sd.depth + 1;
   const uint64_t m = sd.end - sd.begin;
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     atomicAdd(&a.hdr->keys_partitioned, m);
     atomicAdd(&a.hdr->tiles, 2ull * sd.ntiles);
     atomicAdd(&a.hdr->segments, 1ull);
     atomicAdd(&a.hdr->kway_ranges, 1ull);
     atomicMax(&a.hdr->max_depth, (unsigned long long)d1);
   }
-  if (__ldcg(&kw.start[0]) != sd.begin || __ldcg(&kw.start[KWAY]) != sd.end) {   // guard
+  unsigned long long handed = 0, setup = 0;
+  bool nokway = false;
+  if (tid < K) {
+    const uint64_t cb = __ldcg(&kw.start[tid]), ce = __ldcg(&kw.start[tid + 1]);
+    if (ce < cb || cb < sd.begin || ce > sd.end) {
+      guard_failed(a, GUARD_BOUNDS);
+    } else if (ce > cb) {
+      const uint64_t mc = ce - cb;
+      if (mc <= a.leaf_cutoff) {
+        const bool warp = mc <= WARP_LEAF_MAX;
+        const unsigned long long i = atomicAdd(warp ? &a.hdr->n_leaf_warp : &a.hdr->n_leaf_block, 1ull);
+        if (i < (warp ? a.cap_leaf_warp : a.cap_leaf_block)) {
+          (warp ? a.leaf_warp : a.leaf_block)[i] = LeafEntry{cb, (unsigned)mc, parity};
+          atomicAdd(warp ? &a.hdr->leaves_warp : &a.hdr->leaves_block, 1ull);
+          atomicAdd(&a.hdr->leaf_keys, mc);
+        } else {
+          raise_error(a, ERR_INTERNAL);
+        }
+        handed = mc;
+      } else if (d1 >= sd.depth_limit) {
+        const unsigned long long i = atomicAdd(&a.hdr->n_fb, 1ull);
+        if (i < a.cap_fb) {
+          a.fb[i] = LeafEntry{cb, (unsigned)mc, parity};
+          atomicAdd(&a.hdr->fallback_ranges, 1ull);
+          atomicAdd(&a.hdr->fallback_keys, mc);
+        } else {
+          raise_error(a, ERR_INTERNAL);
+        }
+        handed = mc;
+      } else {
+        setup = 1;
+        nokway = mc == m;   // the split made no progress: split this one in two
+      }
+    }
+  }
+  unsigned long long nsetup, handed_total;
+  const unsigned long long pos = block_excl_scan(setup, s_w, nsetup);
+  block_excl_scan(handed, s_w, handed_total);
+  __shared__ unsigned long long s_q0;
+  if (tid == 0) {
+    unsigned long long q0 = nsetup ? atomicAdd(&a.hdr->tail, nsetup) : 0ull;
+    if (nsetup && q0 + nsetup > a.cap_q) {
+      raise_error(a, ERR_INTERNAL);
+      q0 = ~0ull;
+    }
+    s_q0 = q0;
+  }
+  __syncthreads();
+  if (setup && s_q0 != ~0ull)
+    st_release(&a.items[s_q0 + pos], ITEM_VALID | ((unsigned long long)sid << 32) | ITEM_SETUP |
+                                         (nokway ? ITEM_NOKWAY : 0ull) | tid);
+  __syncthreads();
+  if (tid == 0 && handed_total) atomicAdd(&a.hdr->remaining, 0ull - handed_total);
+}
+
+// A setup item: child j of range pd (id psid) becomes a partitioned range.
+template <int KB, unsigned R>
+__device__ void setup_child(const SortArgs &a, const SegDesc &pd, unsigned psid, unsigned j, bool allow_kway,
+                            void *scratch, RangeScratch &rs) {
+  uint64_t cb, ce;
+  if (pd.flags & SEG_KWAY) {
+    const KwayDesc &kw = a.kw[pd.piv_lo];
+    cb = __ldcg(&kw.start[j]);
+    ce = __ldcg(&kw.start[j + 1]);
+  } else {
+    const uint64_t L = ld_relaxed(&a.segs[psid].cursor) & 0xFFFFFFFFull;
+    cb = j ? pd.begin + L : pd.begin;
+    ce = j ? pd.end : pd.begin + L;
+  }
+  const unsigned parity = (pd.flags & SEG_PARITY) ^ 1u;
+  const unsigned d1 = pd.depth + 1, limit = pd.depth_limit;
+  if (ce <= cb || ce > a.n_total) {   // guard (uniform: every thread read the same bounds)
     if (threadIdx.x == 0) guard_failed(a, GUARD_BOUNDS);
     return;
   }
-  uint64_t handed = 0;
-  for (unsigned j = 0; j < KWAY; ++j) {
-    const uint64_t cb = __ldcg(&kw.start[j]), ce = __ldcg(&kw.start[j + 1]);
-    if (ce < cb) {
-      if (threadIdx.x == 0) guard_failed(a, GUARD_BOUNDS);
-      break;
-    }
-    // a bucket holding the whole range made no progress: split it in two
-    handed += child_range<KB>(a, cb, ce, d1, parity, sd.depth_limit, scratch, rs, ce - cb < m);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && handed) atomicAdd(&a.hdr->remaining, (unsigned long long)(0ull - handed));
+  start_range<KB, R>(a, cb, ce, d1, parity, limit, allow_kway, scratch, rs);
 }
 
 // Everything Algorithm 1 does after Partition returned, for range `sd`.
@@ -452,7 +699,7 @@ __device__ void finish_range(const SortArgs &a, const SegDesc &sd, unsigned sid,
   uint64_t handed = 0;
   if (sd.flags & SEG_EXCL) {
     // pivot was one below the repeated maximum p: the right side is all p
-    handed += child_range<KB>(a, b, b + L, d1, parity, sd.depth_limit, scratch, rs);
+    handed += child_range<KB>(a, b, b + L, d1, parity, sd.depth_limit, scratch, rs, sid, 0);
     emit_equal(a, b + L, e - (b + L), parity, rs);
     handed += e - (b + L);
   } else if (L == m) {
@@ -472,8 +719,8 @@ __device__ void finish_range(const SortArgs &a, const SegDesc &sd, unsigned sid,
       make_segment<KB>(a, b, e, d1, parity | SEG_EXCL, pred(p), sd.depth_limit, rs);
     }
   } else {
-    handed += child_range<KB>(a, b, b + L, d1, parity, sd.depth_limit, scratch, rs);
-    handed += child_range<KB>(a, b + L, e, d1, parity, sd.depth_limit, scratch, rs);
+    handed += child_range<KB>(a, b, b + L, d1, parity, sd.depth_limit, scratch, rs, sid, 0);
+    handed += child_range<KB>(a, b + L, e, d1, parity, sd.depth_limit, scratch, rs, sid, 1);
   }
   __syncthreads();
   if (threadIdx.x == 0 && handed) atomicAdd(&a.hdr->remaining, (unsigned long long)(0ull - handed));
@@ -587,93 +834,114 @@ __device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *sw,
   }
 }
 
-// Bucket of a code among the KWAY-1 ascending splitters: the number of
-// splitters strictly below it (keys equal to a splitter take the lower bucket).
-template <class C> __device__ __forceinline__ unsigned bucket_of(const C &k, const C *split) {
-  unsigned bk = 0;
-#pragma unroll
-  for (unsigned step = KWAY / 2; step; step >>= 1)
-    if (lt(split[bk + step - 1], k)) bk += step;
-  return bk;
-}
-
-// One tile of a K-way range. Pass A: per-warp bucket counts (warp-aggregated
-// with __match_any_sync). Counting pass: add the tile's counts to the range's
-// histogram. Scatter pass: reserve the tile's slots in every bucket, then
-// write each key to bucket cursor + warp offset + rank among equal-bucket
-// lanes.
-template <int KB, int CPT, bool RAW>
-__device__ __forceinline__ void kway_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
-                                          unsigned hi, const typename KT<KB>::Code *split, bool scatter,
-                                          KwayDesc &kw, typename KT<KB>::Mem *dst, unsigned *s_wh,
-                                          unsigned long long *s_base) {
+// Counting pass over a K-way tile window: every key adds one to its bucket's
+// shared histogram.
+template <int KB, int KCPT, bool RAW>
+__device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
+                                              unsigned hi, const KwLookup<typename KT<KB>::Code> &cl,
+                                              unsigned *s_hist) {
   using C = typename KT<KB>::Code;
   constexpr unsigned V = 16 / KB;
-  const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned ltm = (1u << lane) - 1u;
-  unsigned *wh = s_wh + warp * KWAY;
-  for (unsigned i = tid; i < NWARP * KWAY; i += NT) s_wh[i] = 0;
-  __syncthreads();
-#pragma unroll 2
-  for (int j = 0; j < CPT; ++j) {
+#pragma unroll
+  for (int j = 0; j < KCPT; ++j) {
+    const unsigned c = threadIdx.x + j * NT;
+    if (c < nwc) {
+      const uint4 q = sw[c];
+      const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
+#pragma unroll
+      for (unsigned v = 0; v < V; ++v) {
+        const unsigned off = 16 * c + v * KB;
+        if (full || (off >= lo && off < hi)) {
+          C k = key_at<KB>(q, v);
+          if (RAW) k = encode<KB>(k, a.codec);
+          atomicAdd(&s_hist[cl(k)], 1u);
+        }
+      }
+    }
+  }
+}
+
+// Scatter pass over a K-way tile window. (1) Each key takes the next rank in
+// its bucket from the shared histogram. (2) One thread per bucket turns the
+// tile's counts into offsets of the bucket-ordered tile and reserves the
+// bucket's slots in the range with one atomic. (3) Keys are staged in bucket
+// order in the second half of the window. (4) The staged tile is written out
+// with consecutive threads on consecutive keys, so each bucket's keys leave
+// as one contiguous run.
+template <int KB, int KCPT, bool RAW>
+__device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
+                                                unsigned hi, const KwLookup<typename KT<KB>::Code> &cl,
+                                                KwayDesc &kw, unsigned stripe, uint64_t rbegin,
+                                                typename KT<KB>::Mem *dst,
+                                                typename KT<KB>::Mem *stage, unsigned char *sb,
+                                                unsigned *s_hist, unsigned short *s_tstart,
+                                                unsigned long long *s_off, unsigned long long *s_w) {
+  using C = typename KT<KB>::Code;
+  constexpr unsigned V = 16 / KB, Q = KCPT * V;
+  const unsigned tid = threadIdx.x, K = cl.K;
+  uint32_t pk[Q];   // rank << 8 | bucket, ~0 for no key
+#pragma unroll
+  for (int j = 0; j < KCPT; ++j) {
     const unsigned c = tid + j * NT;
-    const uint4 q = c < nwc ? sw[c] : make_uint4(0, 0, 0, 0);
-    const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
 #pragma unroll
-    for (unsigned v = 0; v < V; ++v) {
-      const unsigned off = 16 * c + v * KB;
-      const bool valid = full || (off >= lo && off < hi);
-      C k = key_at<KB>(q, v);
-      if (RAW) k = encode<KB>(k, a.codec);
-      const unsigned bk = valid ? bucket_of(k, split) : KWAY;
-      const unsigned peers = __match_any_sync(FULL, bk);
-      if (valid && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&wh[bk], (unsigned)__popc(peers));
+    for (unsigned v = 0; v < V; ++v) pk[j * V + v] = ~0u;
+    if (c < nwc) {
+      const uint4 q = sw[c];
+      const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
+#pragma unroll
+      for (unsigned v = 0; v < V; ++v) {
+        const unsigned off = 16 * c + v * KB;
+        if (full || (off >= lo && off < hi)) {
+          C k = key_at<KB>(q, v);
+          if (RAW) k = encode<KB>(k, a.codec);
+          const unsigned bk = cl(k);
+          pk[j * V + v] = (atomicAdd(&s_hist[bk], 1u) << 8) | bk;
+        }
+      }
     }
   }
   __syncthreads();
-  if (!scatter) {
-    if (tid < KWAY) {
-      unsigned tot = 0;
-#pragma unroll
-      for (int w = 0; w < NWARP; ++w) tot += s_wh[w * KWAY + tid];
-      if (tot) atomicAdd(&kw.count[tid], (unsigned long long)tot);
+  const unsigned cnt = tid < K ? s_hist[tid] : 0u;
+  unsigned long long nkeys;
+  const unsigned long long excl = block_excl_scan(cnt, s_w, nkeys);
+  if (tid < K) {
+    s_tstart[tid] = (unsigned short)excl;
+    unsigned long long off = 0;
+    if (cnt) {
+      const unsigned long long base = rbegin + atomicAdd(&kw.cnt[stripe][tid], cnt);
+      if (base + cnt > __ldcg(&kw.start[tid + 1])) {   // guard: stay inside the bucket
+        guard_failed(a, GUARD_BUCKET);
+        off = ~0ull;
+      } else {
+        off = base - excl;
+      }
     }
-    return;
-  }
-  if (tid < KWAY) {
-    unsigned run = 0;
-#pragma unroll
-    for (int w = 0; w < NWARP; ++w) {
-      const unsigned x = s_wh[w * KWAY + tid];
-      s_wh[w * KWAY + tid] = run;
-      run += x;
-    }
-    unsigned long long base = run ? atomicAdd(&kw.cursor[tid], (unsigned long long)run) : 0ull;
-    if (run && base + run > __ldcg(&kw.start[tid + 1])) {   // guard: stay inside the bucket
-      guard_failed(a, GUARD_BUCKET);
-      base = ~0ull;
-    }
-    s_base[tid] = base;
+    s_off[tid] = off;
+    s_hist[tid] = 0;   // ready for the next tile
   }
   __syncthreads();
-#pragma unroll 2
-  for (int j = 0; j < CPT; ++j) {
+#pragma unroll
+  for (int j = 0; j < KCPT; ++j) {
     const unsigned c = tid + j * NT;
-    const uint4 q = c < nwc ? sw[c] : make_uint4(0, 0, 0, 0);
-    const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
+    if (c < nwc) {
+      const uint4 q = sw[c];
 #pragma unroll
-    for (unsigned v = 0; v < V; ++v) {
-      const unsigned off = 16 * c + v * KB;
-      const bool valid = full || (off >= lo && off < hi);
-      C k = key_at<KB>(q, v);
-      if (RAW) k = encode<KB>(k, a.codec);
-      const unsigned bk = valid ? bucket_of(k, split) : KWAY;
-      const unsigned peers = __match_any_sync(FULL, bk);
-      if (valid && s_base[bk] != ~0ull) dst[s_base[bk] + wh[bk] + __popc(peers & ltm)] = to_mem<KB>(k);
-      __syncwarp();
-      if (valid && lane == (unsigned)(__ffs(peers) - 1)) wh[bk] += __popc(peers);
-      __syncwarp();
+      for (unsigned v = 0; v < V; ++v) {
+        const uint32_t p = pk[j * V + v];
+        if (p != ~0u) {
+          C k = key_at<KB>(q, v);
+          if (RAW) k = encode<KB>(k, a.codec);
+          const unsigned bk = p & 255u, pos = s_tstart[bk] + (p >> 8);
+          stage[pos] = to_mem<KB>(k);
+          sb[pos] = (unsigned char)bk;
+        }
+      }
     }
+  }
+  __syncthreads();
+  for (unsigned p = tid; p < (unsigned)nkeys; p += NT) {
+    const unsigned long long off = s_off[sb[p]];
+    if (off != ~0ull) dst[off + p] = stage[p];
   }
 }
 
@@ -692,9 +960,9 @@ __global__ void k_prep(SortArgs a) {
 
 // Roots of the recursion: one range per segment (or the whole array).
 template <int KB> __global__ void __launch_bounds__(NT) k_seed(SortArgs a) {
+  constexpr unsigned R = kw_sample_r<KB, 8>();
   __shared__ RangeScratch rs;
-  __shared__ __align__(16) unsigned char scratch[KWAY_SAMPLE * sizeof(typename KT<KB>::Code) + 1024 +
-                                                 KWAY * sizeof(typename KT<KB>::Code)];
+  __shared__ __align__(16) unsigned char scratch[kw_scratch_bytes<KB, R>()];
   for (unsigned long long sg = blockIdx.x; sg < a.num_segments; sg += gridDim.x) {
     uint64_t b = 0, e = a.n_total;
     if (a.offsets) {
@@ -724,19 +992,7 @@ template <int KB> __global__ void __launch_bounds__(NT) k_seed(SortArgs a) {
       emit_fallback(a, b, m, SEG_RAW, rs);
     } else {
       if (threadIdx.x == 0) atomicAdd(&a.hdr->remaining, m);
-      using C = typename KT<KB>::Code;
-      bool done = false;
-      if (a.kw && m >= KWAY_MIN) {
-        C *split = (C *)(scratch + KWAY_SAMPLE * sizeof(C) + 1024);
-        if (sample_splitters<KB>(a.keys, b, m, true, a.codec, range_seed(a.seed, b, 0), scratch, split)) {
-          make_kway_segment<KB>(a, b, e, 0, SEG_RAW, limit, split, rs);
-          done = true;
-        }
-      }
-      if (!done) {
-        const auto p = sample_pivot<KB>(a.keys, b, m, true, a.codec, range_seed(a.seed, b, 0), scratch);
-        make_segment<KB>(a, b, e, 0, SEG_RAW, p, limit, rs);
-      }
+      start_range<KB, R>(a, b, e, 0, SEG_RAW, limit, true, scratch, rs);
     }
     __syncthreads();
   }
@@ -754,14 +1010,9 @@ __device__ __forceinline__ void load_desc(const SortArgs &a, unsigned long long 
   for (int k = 0; k < 8; ++k) sw[k] = w[k];
 }
 
-// Loads the splitters of K-way record `kid` (through L2) into shared memory.
-template <int KB>
-__device__ __forceinline__ void load_splitters(const SortArgs &a, unsigned long long kid,
-                                               typename KT<KB>::Code *split) {
-  const KwayDesc &kw = a.kw[kid];
-#pragma unroll
-  for (unsigned j = 0; j < KWAY - 1; ++j)
-    split[j] = code_of<KB>(__ldcg(&kw.split_lo[j]), KB == 16 ? __ldcg(&kw.split_hi[j]) : 0ull);
+// Keys per tile of a range.
+__device__ __forceinline__ unsigned tile_keys_of(const SortArgs &a, const SegDesc &seg) {
+  return (seg.flags & SEG_KWAY) ? a.kw_tile_keys : a.tile_keys;
 }
 
 // Starts the TMA bulk copy of the tile's 16-byte-aligned window into `buf`.
@@ -770,8 +1021,8 @@ __device__ __forceinline__ void load_splitters(const SortArgs &a, unsigned long 
 template <int KB>
 __device__ __forceinline__ void issue_tile(const SortArgs &a, unsigned long long item, const SegDesc &seg,
                                            unsigned char *buf, uint64_t *bar) {
-  const unsigned T = a.tile_keys;
-  const unsigned i = (unsigned)(item & 0x7FFFFFFFu);
+  const unsigned T = tile_keys_of(a, seg);
+  const unsigned i = (unsigned)(item & ITEM_INDEX);
   const uint64_t b = seg.begin, e = seg.end;
   const bool par = seg.flags & SEG_PARITY;
   const unsigned char *src = (const unsigned char *)(par ? a.alt : a.keys);
@@ -789,33 +1040,73 @@ __device__ __forceinline__ void issue_tile(const SortArgs &a, unsigned long long
   bulk_load(buf, (const void *)w0, (uint32_t)(w1 - w0), bar);
 }
 
-// The persistent partition kernel. Per tile: one TMA copy into the shared
-// window, a counting pass, one atomic on the range's write cursors that
-// reserves this tile's slots on both sides (the GPU form of the bidirectional
-// write positions of Sec. 2.1: the order of keys within a side is free, so
-// tiles need not wait for one another), and a scatter pass that writes every
-// key straight from its ballot rank to global memory (each warp store is two
-// contiguous runs). A block needs only the window and few registers, so
-// several blocks per SM keep enough bytes in flight.
+// Thread 0, after a claim: the item goes to s_item, its range descriptor to
+// s_seg (kept while consecutive tiles share a range), and a tile's copy is
+// started. A setup item loads its parent's descriptor and copies nothing.
+template <int KB>
+__device__ __forceinline__ void prepare(const SortArgs &a, unsigned long long item, unsigned long long &s_item,
+                                        SegDesc &s_seg, unsigned &seg_in_smem, int &s_newtree,
+                                        unsigned char *buf, uint64_t *bar) {
+  s_item = item;
+  s_newtree = 0;
+  const unsigned sid = (unsigned)((item >> 32) & 0x7FFFFFFFu);
+  if (item & ITEM_SETUP) {
+    load_desc(a, item, s_seg);
+    seg_in_smem = ~0u;
+    return;
+  }
+  if (sid != seg_in_smem) {
+    load_desc(a, item, s_seg);
+    seg_in_smem = sid;
+    s_newtree = (s_seg.flags & SEG_KWAY) != 0;
+  }
+  issue_tile<KB>(a, item, s_seg, buf, bar);
+}
+
+// The persistent partition kernel. Per two-way tile: one TMA copy into the
+// shared window, a counting pass, one atomic on the range's write cursors
+// that reserves this tile's slots on both sides (the GPU form of the
+// bidirectional write positions of Sec. 2.1: the order of keys within a side
+// is free, so tiles need not wait for one another), and a scatter pass that
+// writes every key straight from its ballot rank to global memory (each warp
+// store is two contiguous runs). K-way tiles count or scatter by bucket
+// (kw_count_tile, kw_scatter_tile); setup items start a child range. A block
+// needs only the window and few registers, so several blocks per SM keep
+// enough bytes in flight.
 template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER_SM) k_partition(SortArgs a) {
   using C = typename KT<KB>::Code;
   using M = typename KT<KB>::Mem;
-  const unsigned T = a.tile_keys;   // <= part_tile_keys(KB, CPT)
+  constexpr int KCPT = kw_cpt(KB, CPT);
+  constexpr unsigned TKW = kw_tile_keys(KB, CPT);
+  constexpr unsigned RS = kw_sample_r<KB, CPT>();
+  static_assert(kw_scratch_bytes<KB, RS>() <= (unsigned)part_window(CPT), "setup sample fits the window");
+  constexpr unsigned PIV_BYTES = SAMPLE * sizeof(C) + SAMPLE / (64 / KB) * 8;
+  constexpr unsigned LOOKUP_BYTES = KW_MAX * sizeof(C) + KW_TABLE * 2;
+  constexpr unsigned AUX = PIV_BYTES > LOOKUP_BYTES ? PIV_BYTES : LOOKUP_BYTES;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t s_bar;
   __shared__ SegDesc s_seg, s_fseg;
   __shared__ unsigned long long s_item, s_ticket;
   __shared__ unsigned s_fsid, s_fphase;
-  __shared__ int s_go, s_go2, s_fin;
+  __shared__ int s_go, s_go2, s_fin, s_newtree;
   __shared__ unsigned s_wL[NWARP], s_wV[NWARP], s_bL[NWARP], s_bR[NWARP];
   __shared__ unsigned long long s_cur;
   __shared__ RangeScratch rs;
-  __shared__ __align__(16) unsigned char s_sample[KWAY_SAMPLE * sizeof(C) + 1024 + KWAY * sizeof(C)];
-  __shared__ C s_split[KWAY];
-  __shared__ unsigned s_wh[NWARP * KWAY];
-  __shared__ unsigned long long s_base[KWAY];
+  // finishers' pivot samples, and the bucket lookup of K-way tiles (reloaded
+  // after a finisher ran)
+  __shared__ __align__(16) unsigned char s_aux[AUX];
+  __shared__ unsigned s_hist[KW_MAX];
+  __shared__ unsigned short s_tstart[KW_MAX];
+  __shared__ unsigned long long s_off[KW_MAX];
+  __shared__ unsigned long long s_w[NWARP];
+  __shared__ unsigned char s_sb[TKW];
+  __shared__ unsigned s_shift;
+  C *s_split = (C *)s_aux;
+  unsigned short *s_table = (unsigned short *)(s_aux + KW_MAX * sizeof(C));
+  M *stage = (M *)(smem + part_window(CPT) / 2);
 
   const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (unsigned j = tid; j < KW_MAX; j += NT) s_hist[j] = 0;
   if (tid == 0) {
     mbar_init(&s_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -827,10 +1118,14 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
   // two round trips overlap.
   unsigned seg_in_smem = ~0u, pend_sid = ~0u, pend_nt = 0, pend_phase = 0;
   uint32_t pend_prev = 0;
+  // the next ticket, claimed while the current tile is processed
+  bool nclaimed = false;
+  unsigned long long nticket = 0;
 
   for (;;) {
     if (tid == 0) {
-      const unsigned long long t = atomicAdd(&a.hdr->head, 1ull);
+      const unsigned long long t = nclaimed ? nticket : atomicAdd(&a.hdr->head, 1ull);
+      nclaimed = false;
       unsigned long long item = 0;
       const bool have = probe_ticket(a, t, item);
       int fin = 0;
@@ -845,25 +1140,16 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
         pend_sid = ~0u;
       }
       s_fin = fin;
-      if (have) {
-        s_item = item;
-        const unsigned sid = (unsigned)((item >> 32) & 0x7FFFFFFFu);
-        if (sid != seg_in_smem) {
-          load_desc(a, item, s_seg);
-          if (s_seg.flags & SEG_KWAY) load_splitters<KB>(a, s_seg.piv_lo, s_split);
-          seg_in_smem = sid;
-        }
-        issue_tile<KB>(a, item, s_seg, smem, &s_bar);
-      }
+      if (have) prepare<KB>(a, item, s_item, s_seg, seg_in_smem, s_newtree, smem, &s_bar);
       s_go = have;
       s_ticket = t;
     }
     __syncthreads();
     // the previous tile finished its range: the rest of Algorithm 1 for it
     if (s_fin) {
-      if (!(s_fseg.flags & SEG_KWAY)) finish_range<KB>(a, s_fseg, s_fsid, s_sample, rs);
-      else if (!s_fphase) finish_kway_count(a, s_fseg, s_fsid, rs);
-      else finish_kway_scatter<KB>(a, s_fseg, s_fsid, s_sample, rs);
+      if (!(s_fseg.flags & SEG_KWAY)) finish_range<KB>(a, s_fseg, s_fsid, s_aux, rs);
+      else if (!s_fphase) finish_kway_count(a, s_fseg, s_fsid, rs, s_w);
+      else finish_kway_scatter(a, s_fseg, s_fsid, s_w);
     }
     if (!s_go) {
       // the claimed item is not published yet (it may come from the range
@@ -873,20 +1159,31 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
       if (tid == 0) {
         unsigned long long item = 0;
         const int go = wait_ticket(a, s_ticket, item);
-        if (go) {
-          s_item = item;
-          const unsigned sid = (unsigned)((item >> 32) & 0x7FFFFFFFu);
-          if (sid != seg_in_smem) {
-            load_desc(a, item, s_seg);
-            if (s_seg.flags & SEG_KWAY) load_splitters<KB>(a, s_seg.piv_lo, s_split);
-            seg_in_smem = sid;
-          }
-          issue_tile<KB>(a, item, s_seg, smem, &s_bar);
-        }
+        if (go) prepare<KB>(a, item, s_item, s_seg, seg_in_smem, s_newtree, smem, &s_bar);
         s_go2 = go;
       }
       __syncthreads();
       if (!s_go2) break;
+    }
+
+    const unsigned long long item = s_item;
+    const SegDesc &sg = s_seg;
+    const unsigned sid = (unsigned)((item >> 32) & 0x7FFFFFFFu);
+    const unsigned i = (unsigned)(item & ITEM_INDEX);
+    if (item & ITEM_SETUP) {
+      // no copy was started: the window is free scratch for the sample
+      setup_child<KB, RS>(a, sg, sid, i, (item & ITEM_NOKWAY) == 0, smem, rs);
+      continue;
+    }
+    const bool kway = sg.flags & SEG_KWAY;
+    if (kway && (s_newtree || s_fin)) {
+      const KwayDesc &kw = a.kw[sg.piv_lo];
+      for (unsigned j = tid; j < KW_MAX; j += NT)
+        s_split[j] = code_of<KB>(__ldcg(&kw.split_lo[j]), KB == 16 ? __ldcg(&kw.split_hi[j]) : 0ull);
+      for (unsigned j = tid; j < KW_TABLE / 2; j += NT)
+        ((unsigned *)s_table)[j] = __ldcg((const unsigned *)kw.table + j);
+      if (tid == 0) s_shift = __ldcg(&kw.shift);
+      __syncthreads();
     }
     {
       unsigned it = 0;
@@ -898,14 +1195,15 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
       }
       phase ^= 1;
     }
+    if (tid == 0) {   // its result is first used at the next claim
+      nticket = atomicAdd(&a.hdr->head, 1ull);
+      nclaimed = true;
+    }
 
-    const SegDesc &sg = s_seg;
-    const unsigned sid = (unsigned)((s_item >> 32) & 0x7FFFFFFFu);
-    const unsigned i = (unsigned)(s_item & 0x7FFFFFFFu);
-    const bool phase1 = (s_item & ITEM_PHASE) != 0;
+    const bool phase1 = (item & ITEM_PHASE) != 0;
+    const unsigned T = kway ? TKW : a.tile_keys;
     const uint64_t b = sg.begin, e = sg.end;
     const bool par = sg.flags & SEG_PARITY, raw = sg.flags & SEG_RAW;
-    const C piv = code_of<KB>(sg.piv_lo, sg.piv_hi);
     const unsigned char *src = (const unsigned char *)(par ? a.alt : a.keys);
     M *dst = (M *)(par ? a.keys : a.alt);
     const uint64_t t0 = b + (uint64_t)i * T;
@@ -916,10 +1214,32 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
     const unsigned lo = (unsigned)(g0 - w0), hi = (unsigned)(g1 - w0);
     const uint4 *sw = (const uint4 *)smem;
 
-    if (sg.flags & SEG_KWAY) {
+    if (kway) {
       KwayDesc &kw = a.kw[sg.piv_lo];
-      if (raw) kway_tile<KB, CPT, true>(a, sw, nwc, lo, hi, s_split, phase1, kw, dst, s_wh, s_base);
-      else kway_tile<KB, CPT, false>(a, sw, nwc, lo, hi, s_split, phase1, kw, dst, s_wh, s_base);
+      const unsigned kbits = (unsigned)sg.piv_hi;
+      KwLookup<C> cl;
+      cl.split = s_split;
+      cl.table = s_table;
+      cl.K = 1u << kbits;
+      cl.s1 = s_split[1];
+      cl.sk = s_split[cl.K - 1];
+      cl.sh = s_shift;
+      if (!phase1) {
+        if (raw) kw_count_tile<KB, KCPT, true>(a, sw, nwc, lo, hi, cl, s_hist);
+        else kw_count_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, cl, s_hist);
+        __syncthreads();
+        if (tid < (1u << kbits)) {
+          const unsigned x = s_hist[tid];
+          if (x) atomicAdd(&kw.cnt[i % KW_STRIPES][tid], x);
+          s_hist[tid] = 0;
+        }
+      } else if (raw) {
+        kw_scatter_tile<KB, KCPT, true>(a, sw, nwc, lo, hi, cl, kw, i % KW_STRIPES, b, dst, stage,
+                                        s_sb, s_hist, s_tstart, s_off, s_w);
+      } else {
+        kw_scatter_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, cl, kw, i % KW_STRIPES, b, dst, stage,
+                                         s_sb, s_hist, s_tstart, s_off, s_w);
+      }
       fence_proxy_async_smem();   // the next TMA copy reuses the window
       __syncthreads();
       if (tid == 0) {
@@ -931,6 +1251,7 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
       continue;
     }
 
+    const C piv = code_of<KB>(sg.piv_lo, sg.piv_hi);
     // ---- pass 1: per-warp counts of left and valid keys
     unsigned nL = 0, nV = 0;
     int anyLt = 0;

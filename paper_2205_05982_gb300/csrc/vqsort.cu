@@ -54,7 +54,7 @@ int64_t g_spin_limit = 1 << 22;
 int64_t g_test_stall = 0;
 int64_t g_tile_bytes = 0;     // 0: 32 KiB partition tile windows
 int64_t g_leaf_threads = 0;   // 0: 16 keys per thread at the cutoff
-int64_t g_kway = 1;           // K-way levels for ranges of >= KWAY_MIN keys
+int64_t g_kway = 1;           // K-way levels for ranges of >= 4 x the leaf cutoff
 
 int tile_cpt() {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -80,7 +80,6 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_limit, bool with_alt,
                    int cpt) {
-  const uint64_t T = part_tile_keys(kb, cpt);
   const uint64_t lg = floor_log2_u64(n < 2 ? 2 : n);
   uint64_t levels = 2 * lg + 4;
   if (depth_limit >= 0 && (uint64_t)depth_limit > levels) levels = (uint64_t)depth_limit;
@@ -88,9 +87,13 @@ Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_lim
   const uint64_t per_level = n / (C + 1ull) + 1;
   Layout L{};
   const uint64_t cap_segs = (levels + 1) * per_level + 16;
-  // a K-way range runs its tiles twice (counting pass, scatter pass)
-  const uint64_t cap_q = (levels + 1) * (2 * ((n + T - 1) / T) + per_level) + 16;
-  const uint64_t cap_kw = (levels + 1) * (n / KWAY_MIN + 1) + S + 16;
+  // Per level: a K-way range runs its (smaller) tiles twice, counting and
+  // scattering; every range may add a partial tile per pass and one setup item.
+  const uint64_t TK = kw_tile_keys(kb, cpt);
+  const uint64_t cap_q = (levels + 1) * (2 * (n / TK + 1) + 3 * per_level) + 2 * S + 16;
+  // K-way records: ranges of >= 4C keys; when they run out, ranges are split
+  // in two instead
+  const uint64_t cap_kw = 2 * (n / (4ull * C) + 1) + 64;
   const uint64_t cap_lw = 2 * cap_segs + S + 16;
   const uint64_t cap_lb = n / 512 + n / C + 2 * cap_segs + S + 16;
   const uint64_t cap_fb = n / (C + 1ull) + S + 16;
@@ -279,6 +282,9 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   a.cap_leaf_block = L.cap_lb;
   a.cap_fb = L.cap_fb;
   a.tile_keys = part_tile_keys(kb, cpt);
+  a.kw_tile_keys = kw_tile_keys(kb, cpt);
+  a.kw_min_keys = 4 * C;
+  a.kw_target = C / 4;
   a.tile_cpt = (unsigned)cpt;
   a.leaf_threads = kb == 16 ? 0u : (unsigned)leaf_threads;
   a.leaf_cutoff = C;

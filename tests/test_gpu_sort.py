@@ -173,20 +173,28 @@ def test_explicit_workspace_and_graph_capture(vq, oracle_mod):
         assert same_bits(to_host(t, "u64", src), oracle_mod.sort(src, "u64"))
 
 
+@pytest.mark.parametrize("kway", (0, 1))
 @pytest.mark.parametrize("dtype", ("u32", "i64", "f64", "u128"))
 @pytest.mark.parametrize("limit", (0, 1, 3))
-def test_depth_bound_fallback(vq, oracle_mod, dtype, limit):
+def test_depth_bound_fallback(vq, oracle_mod, dtype, limit, kway):
     """Forcing the depth bound low sends ranges to the merge fallback; the
-    result must not change."""
+    result must not change. With K-way levels one level may already reach
+    the leaves, so only the two-way run must reach the fallback."""
     vq.set_option("depth_limit", limit)
+    vq.set_option("kway", kway)
     try:
         for dist in ("uniform", "organpipe", "distinct16"):
-            a = make(dtype, 200_003, dist, seed=9)
+            n = 200_003
+            a = make(dtype, n, dist, seed=9)
             check_sort(vq, oracle_mod, dtype, a, True)
             st = vq.stats()
-            assert st["fallback_ranges"] >= 1
+            assert st["leaf_keys"] + st["equal_keys"] + st["fallback_keys"] == n
+            assert st["max_depth"] <= limit
+            if not kway or limit == 0:
+                assert st["fallback_ranges"] >= 1
     finally:
         vq.set_option("depth_limit", -1)
+        vq.set_option("kway", 1)
 
 
 @pytest.mark.parametrize("cutoff", (1024, 4096, 16384))
@@ -274,3 +282,51 @@ def test_kway_mid_sizes_with_workspace(vq, oracle_mod, n):
         assert vq.last_device_status(ws) == 0, vq.stats(ws)
         assert vq.stats(ws)["guard"] == 0
         assert same_bits(to_host(t, "u64", a), want)
+
+
+@pytest.mark.parametrize("dtype,n", [
+    ("u64", 32_768), ("u64", 50_000), ("u64", 100_003), ("u64", 200_000), ("u64", 3_000_017),
+    ("u32", 65_536), ("u32", 1_000_003), ("u16", 70_001), ("u16", 5_000_011),
+    ("u128", 16_384), ("u128", 700_001), ("kv64", 400_009), ("f64", 20_000_003)])
+def test_kway_bucket_counts(vq, oracle_mod, dtype, n):
+    """Range sizes that give 16, 32, ..., 256 buckets (about a quarter of the
+    leaf cutoff per bucket), and sizes whose buckets are split again, K ways
+    or in two."""
+    a = make(dtype, n, "uniform", seed=n % 1009)
+    check_sort(vq, oracle_mod, dtype, a, True)
+    st = vq.stats()
+    assert st["kway_ranges"] >= 1
+    assert st["keys_counted"] >= n            # the root range was counted
+    assert st["leaf_keys"] + st["equal_keys"] + st["fallback_keys"] == n
+
+
+@pytest.mark.parametrize("dtype", ("u16", "u32", "u64", "u128"))
+def test_kway_small_tile_window(vq, oracle_mod, dtype):
+    """16 KiB tile windows: K-way tiles of half the size, a smaller splitter
+    sample."""
+    vq.set_option("tile_bytes", 16384)
+    try:
+        a = make(dtype, 2_000_003, "uniform", seed=3)
+        check_sort(vq, oracle_mod, dtype, a, True)
+        assert vq.stats()["kway_ranges"] >= 1
+        check_sort(vq, oracle_mod, dtype, a, False)
+    finally:
+        vq.set_option("tile_bytes", 0)
+
+
+@pytest.mark.parametrize("dtype", ("u32", "u64", "kv64"))
+def test_segmented_with_kway_roots(vq, oracle_mod, dtype):
+    """CSR segments large enough to be split K ways next to small ones."""
+    sizes = inputs.segment_sizes(60, 16, 2_000_000, seed=8)
+    sizes[::7] = 0
+    off = inputs.offsets_from_sizes(sizes)
+    n = int(off[-1])
+    a = inputs.kv_pairs(n, seed=8) if dtype == "kv64" else inputs.make(dtype, n, "uniform", seed=8)
+    want = oracle_mod.sort_segmented(a, off, dtype, False)
+    t = to_dev(a, dtype)
+    vq.sort_segmented_(t, off.astype(np.int64), dtype, descending=True)
+    got = to_host(t, dtype, a)
+    assert vq.last_device_status() == 0
+    st = vq.stats()
+    assert st["guard"] == 0 and st["kway_ranges"] >= 1
+    assert same_bits(got, want), first_mismatch(got, want)
