@@ -180,9 +180,10 @@ typedef struct vq_stats {
   uint64_t max_depth;            /* deepest partition level reached */
   uint64_t device_status;        /* vq_status latched on the device */
   uint64_t keys_counted;         /* keys read by K-way counting passes */
-  uint64_t kway_ranges;          /* ranges split 16 ways */
+  uint64_t kway_ranges;          /* ranges split K ways (16..256 buckets) */
   uint64_t guard;                /* first failed device bounds guard (0: none); a failed guard
                                     skips the access and latches VQ_ERR_INTERNAL */
+  uint64_t partition_blocks;     /* thread blocks of the persistent partition kernel */
 } vq_stats;
 vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out);
 
@@ -202,7 +203,8 @@ typedef enum vq_option {
   VQ_OPT_TEST_STALL = 4,    /* 1: the root range never publishes its children, so every
                                block's bounded wait for work runs out and the sort reports
                                VQ_ERR_TIMEOUT (test of the bounded-wait path; never hangs) */
-  VQ_OPT_TILE_BYTES = 5,    /* 0 or 32768: 32 KiB partition tiles (default); 16384: 16 KiB */
+  VQ_OPT_TILE_BYTES = 5,    /* partition tile window: 16384, 32768 or 65536 bytes; 0 (default):
+                               64 KiB for 8- and 16-byte keys, 32 KiB for narrower keys */
   VQ_OPT_LEAF_THREADS = 6,  /* 0: block leaves use cutoff/16 threads (16 keys per thread);
                                256, 512 or 1024: that many threads, so cutoff/threads keys
                                per thread (at most 16); ignored for 16-byte keys */

@@ -43,7 +43,8 @@ class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in (
         "keys_partitioned", "tiles", "segments", "leaves_warp", "leaves_block", "leaf_keys",
         "equal_ranges", "equal_keys", "degenerate", "fallback_ranges", "fallback_keys",
-        "max_depth", "device_status", "keys_counted", "kway_ranges", "guard")]
+        "max_depth", "device_status", "keys_counted", "kway_ranges", "guard",
+        "partition_blocks")]
 
 
 _lib = None

@@ -63,7 +63,7 @@ def candidates(dtype: str) -> list[dict]:
     out = []
     kb = KEY_BYTES[dtype]
     cut_max = 4096 if kb == 16 else 16384
-    for tile, cut, thr in itertools.product((16384, 32768), (2048, 4096, 8192, 16384), (0, 256, 512, 1024)):
+    for tile, cut, thr in itertools.product((16384, 32768, 65536), (2048, 4096, 8192, 16384), (0, 256, 512, 1024)):
         if cut > cut_max:
             continue
         if kb == 16 and thr:

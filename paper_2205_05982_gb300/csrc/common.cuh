@@ -276,7 +276,8 @@ struct Header {
   unsigned long long keys_counted; // keys read by K-way counting passes (statistics)
   unsigned long long kway_ranges;  // ranges split K ways (statistics)
   unsigned long long guard;        // first failed bounds guard (GUARD_*), 0 if none
-  unsigned long long pad[3];
+  unsigned long long part_grid;    // blocks of the partition kernel (statistics)
+  unsigned long long pad[2];
 };
 static_assert(sizeof(Header) % 64 == 0, "header size");
 
@@ -370,6 +371,7 @@ struct SortArgs {
   unsigned long long *items;
   LeafEntry *leaf_warp, *leaf_block, *fb;
   KwayDesc *kw;                        // K-way range records (null: K-way levels off)
+  unsigned char *kw_ids;               // bucket of each key, written by K-way counting passes
   const unsigned long long *offsets;   // CSR offsets or null (one segment)
   unsigned long long n_total;
   unsigned long long num_segments;

@@ -10,12 +10,14 @@
 namespace vq {
 
 // Partition kernel geometry: 256 threads, CPT chunks of 16 bytes per thread
-// (CPT = 8: 32 KiB tile windows, the default; CPT = 4: 16 KiB windows).
+// (CPT = 8: 32 KiB tile windows, the default; CPT = 4: 16 KiB windows;
+// CPT = 16: 64 KiB windows).
 constexpr int PART_NT = 256;
 constexpr int PART_CPT = 8;                            // default
-constexpr int PART_BLOCKS_PER_SM = 5;
+// blocks per SM the kernel is built for (shared memory allows this many)
+__host__ __device__ constexpr int part_blocks_per_sm(int cpt) { return cpt >= 16 ? 3 : 5; }
 __host__ __device__ constexpr int part_window(int cpt) { return PART_NT * cpt * 16; }
-__host__ __device__ constexpr int part_smem(int cpt) { return part_window(cpt) + 128; }
+__host__ __device__ constexpr int part_smem(int cpt) { return part_window(cpt); }
 // Tile keys: the tile plus its 16-byte misalignment fits the window.
 __host__ __device__ constexpr unsigned part_tile_keys(int kb, int cpt = PART_CPT) {
   return (unsigned)((part_window(cpt) - 16) / kb);

@@ -839,7 +839,7 @@ __device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *sw,
 template <int KB, int KCPT, bool RAW>
 __device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
                                               unsigned hi, const KwLookup<typename KT<KB>::Code> &cl,
-                                              unsigned *s_hist) {
+                                              unsigned *s_hist, unsigned char *ids) {
   using C = typename KT<KB>::Code;
   constexpr unsigned V = 16 / KB;
 #pragma unroll
@@ -854,7 +854,9 @@ __device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *sw
         if (full || (off >= lo && off < hi)) {
           C k = key_at<KB>(q, v);
           if (RAW) k = encode<KB>(k, a.codec);
-          atomicAdd(&s_hist[cl(k)], 1u);
+          const unsigned bk = cl(k);
+          atomicAdd(&s_hist[bk], 1u);
+          ids[(off - lo) / KB] = (unsigned char)bk;   // for the scatter pass
         }
       }
     }
@@ -862,7 +864,8 @@ __device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *sw
 }
 
 // Scatter pass over a K-way tile window. (1) Each key takes the next rank in
-// its bucket from the shared histogram. (2) One thread per bucket turns the
+// its bucket (stored by the counting pass, copied to s_ids) from the shared
+// histogram. (2) One thread per bucket turns the
 // tile's counts into offsets of the bucket-ordered tile and reserves the
 // bucket's slots in the range with one atomic. (3) Keys are staged in bucket
 // order in the second half of the window. (4) The staged tile is written out
@@ -870,15 +873,15 @@ __device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *sw
 // as one contiguous run.
 template <int KB, int KCPT, bool RAW>
 __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
-                                                unsigned hi, const KwLookup<typename KT<KB>::Code> &cl,
+                                                unsigned hi, const unsigned char *s_ids, unsigned K,
                                                 KwayDesc &kw, unsigned stripe, uint64_t rbegin,
                                                 typename KT<KB>::Mem *dst,
                                                 typename KT<KB>::Mem *stage, unsigned char *sb,
-                                                unsigned *s_hist, unsigned short *s_tstart,
-                                                unsigned long long *s_off, unsigned long long *s_w) {
+                                                unsigned *s_hist, unsigned short *s_tstart, unsigned *s_off,
+                                                unsigned long long *s_w) {
   using C = typename KT<KB>::Code;
   constexpr unsigned V = 16 / KB, Q = KCPT * V;
-  const unsigned tid = threadIdx.x, K = cl.K;
+  const unsigned tid = threadIdx.x;
   uint32_t pk[Q];   // rank << 8 | bucket, ~0 for no key
 #pragma unroll
   for (int j = 0; j < KCPT; ++j) {
@@ -892,9 +895,7 @@ __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *
       for (unsigned v = 0; v < V; ++v) {
         const unsigned off = 16 * c + v * KB;
         if (full || (off >= lo && off < hi)) {
-          C k = key_at<KB>(q, v);
-          if (RAW) k = encode<KB>(k, a.codec);
-          const unsigned bk = cl(k);
+          const unsigned bk = s_ids[(off - lo) / KB];
           pk[j * V + v] = (atomicAdd(&s_hist[bk], 1u) << 8) | bk;
         }
       }
@@ -906,14 +907,15 @@ __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *
   const unsigned long long excl = block_excl_scan(cnt, s_w, nkeys);
   if (tid < K) {
     s_tstart[tid] = (unsigned short)excl;
-    unsigned long long off = 0;
+    // staged position p of this bucket goes to rbegin + off + p
+    unsigned off = 0;
     if (cnt) {
-      const unsigned long long base = rbegin + atomicAdd(&kw.cnt[stripe][tid], cnt);
-      if (base + cnt > __ldcg(&kw.start[tid + 1])) {   // guard: stay inside the bucket
+      const unsigned rel = atomicAdd(&kw.cnt[stripe][tid], cnt);
+      if (rbegin + rel + cnt > __ldcg(&kw.start[tid + 1])) {   // guard: stay inside the bucket
         guard_failed(a, GUARD_BUCKET);
-        off = ~0ull;
+        off = ~0u;
       } else {
-        off = base - excl;
+        off = rel - (unsigned)excl;   // rel >= excl: earlier buckets fill the tile's first slots
       }
     }
     s_off[tid] = off;
@@ -939,9 +941,10 @@ __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *
     }
   }
   __syncthreads();
+  typename KT<KB>::Mem *out = dst + rbegin;
   for (unsigned p = tid; p < (unsigned)nkeys; p += NT) {
-    const unsigned long long off = s_off[sb[p]];
-    if (off != ~0ull) dst[off + p] = stage[p];
+    const unsigned off = s_off[sb[p]];
+    if (off != ~0u) out[off + p] = stage[p];
   }
 }
 
@@ -1017,8 +1020,10 @@ __device__ __forceinline__ unsigned tile_keys_of(const SortArgs &a, const SegDes
 
 // Starts the TMA bulk copy of the tile's 16-byte-aligned window into `buf`.
 // The window may include up to 15 bytes on each side that belong to
-// neighbouring ranges; they are never used (and never cross a page).
-template <int KB>
+// neighbouring ranges; they are never used (and never cross a page). A K-way
+// scatter tile also copies its keys' buckets (one byte each, aligned the same
+// way) into the second half of the window, which is free until staging.
+template <int KB, int CPT>
 __device__ __forceinline__ void issue_tile(const SortArgs &a, unsigned long long item, const SegDesc &seg,
                                            unsigned char *buf, uint64_t *bar) {
   const unsigned T = tile_keys_of(a, seg);
@@ -1036,6 +1041,14 @@ __device__ __forceinline__ void issue_tile(const SortArgs &a, unsigned long long
   const uintptr_t g0 = (uintptr_t)(src + t0 * KB), g1 = g0 + (uintptr_t)cnt * KB;
   const uintptr_t w0 = g0 & ~(uintptr_t)15, w1 = (g1 + 15) & ~(uintptr_t)15;
   fence_proxy_async_global();
+  if ((seg.flags & SEG_KWAY) && (item & ITEM_PHASE)) {
+    const uintptr_t i0 = (uintptr_t)(a.kw_ids + t0) & ~(uintptr_t)15;
+    const uintptr_t i1 = ((uintptr_t)(a.kw_ids + t0 + cnt) + 15) & ~(uintptr_t)15;
+    mbar_arrive_expect_tx(bar, (uint32_t)((w1 - w0) + (i1 - i0)));
+    bulk_load(buf, (const void *)w0, (uint32_t)(w1 - w0), bar);
+    bulk_load(buf + part_window(CPT) / 2, (const void *)i0, (uint32_t)(i1 - i0), bar);
+    return;
+  }
   mbar_arrive_expect_tx(bar, (uint32_t)(w1 - w0));
   bulk_load(buf, (const void *)w0, (uint32_t)(w1 - w0), bar);
 }
@@ -1043,7 +1056,7 @@ __device__ __forceinline__ void issue_tile(const SortArgs &a, unsigned long long
 // Thread 0, after a claim: the item goes to s_item, its range descriptor to
 // s_seg (kept while consecutive tiles share a range), and a tile's copy is
 // started. A setup item loads its parent's descriptor and copies nothing.
-template <int KB>
+template <int KB, int CPT>
 __device__ __forceinline__ void prepare(const SortArgs &a, unsigned long long item, unsigned long long &s_item,
                                         SegDesc &s_seg, unsigned &seg_in_smem, int &s_newtree,
                                         unsigned char *buf, uint64_t *bar) {
@@ -1060,7 +1073,7 @@ __device__ __forceinline__ void prepare(const SortArgs &a, unsigned long long it
     seg_in_smem = sid;
     s_newtree = (s_seg.flags & SEG_KWAY) != 0;
   }
-  issue_tile<KB>(a, item, s_seg, buf, bar);
+  issue_tile<KB, CPT>(a, item, s_seg, buf, bar);
 }
 
 // The persistent partition kernel. Per two-way tile: one TMA copy into the
@@ -1073,7 +1086,8 @@ __device__ __forceinline__ void prepare(const SortArgs &a, unsigned long long it
 // (kw_count_tile, kw_scatter_tile); setup items start a child range. A block
 // needs only the window and few registers, so several blocks per SM keep
 // enough bytes in flight.
-template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER_SM) k_partition(SortArgs a) {
+template <int KB, int CPT>
+__global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortArgs a) {
   using C = typename KT<KB>::Code;
   using M = typename KT<KB>::Mem;
   constexpr int KCPT = kw_cpt(KB, CPT);
@@ -1097,7 +1111,7 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
   __shared__ __align__(16) unsigned char s_aux[AUX];
   __shared__ unsigned s_hist[KW_MAX];
   __shared__ unsigned short s_tstart[KW_MAX];
-  __shared__ unsigned long long s_off[KW_MAX];
+  __shared__ unsigned s_off[KW_MAX];
   __shared__ unsigned long long s_w[NWARP];
   __shared__ unsigned char s_sb[TKW];
   __shared__ unsigned s_shift;
@@ -1107,6 +1121,7 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
 
   const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (unsigned j = tid; j < KW_MAX; j += NT) s_hist[j] = 0;
+  if (blockIdx.x == 0 && tid == 0) a.hdr->part_grid = gridDim.x;
   if (tid == 0) {
     mbar_init(&s_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1140,7 +1155,7 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
         pend_sid = ~0u;
       }
       s_fin = fin;
-      if (have) prepare<KB>(a, item, s_item, s_seg, seg_in_smem, s_newtree, smem, &s_bar);
+      if (have) prepare<KB, CPT>(a, item, s_item, s_seg, seg_in_smem, s_newtree, smem, &s_bar);
       s_go = have;
       s_ticket = t;
     }
@@ -1159,7 +1174,7 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
       if (tid == 0) {
         unsigned long long item = 0;
         const int go = wait_ticket(a, s_ticket, item);
-        if (go) prepare<KB>(a, item, s_item, s_seg, seg_in_smem, s_newtree, smem, &s_bar);
+        if (go) prepare<KB, CPT>(a, item, s_item, s_seg, seg_in_smem, s_newtree, smem, &s_bar);
         s_go2 = go;
       }
       __syncthreads();
@@ -1225,20 +1240,23 @@ template <int KB, int CPT> __global__ void __launch_bounds__(NT, PART_BLOCKS_PER
       cl.sk = s_split[cl.K - 1];
       cl.sh = s_shift;
       if (!phase1) {
-        if (raw) kw_count_tile<KB, KCPT, true>(a, sw, nwc, lo, hi, cl, s_hist);
-        else kw_count_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, cl, s_hist);
+        if (raw) kw_count_tile<KB, KCPT, true>(a, sw, nwc, lo, hi, cl, s_hist, a.kw_ids + t0);
+        else kw_count_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, cl, s_hist, a.kw_ids + t0);
         __syncthreads();
         if (tid < (1u << kbits)) {
           const unsigned x = s_hist[tid];
           if (x) atomicAdd(&kw.cnt[i % KW_STRIPES][tid], x);
           s_hist[tid] = 0;
         }
-      } else if (raw) {
-        kw_scatter_tile<KB, KCPT, true>(a, sw, nwc, lo, hi, cl, kw, i % KW_STRIPES, b, dst, stage,
-                                        s_sb, s_hist, s_tstart, s_off, s_w);
       } else {
-        kw_scatter_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, cl, kw, i % KW_STRIPES, b, dst, stage,
-                                         s_sb, s_hist, s_tstart, s_off, s_w);
+        const unsigned char *s_ids =
+            (const unsigned char *)stage + ((uintptr_t)(a.kw_ids + t0) & 15);   // copied with the keys
+        if (raw)
+          kw_scatter_tile<KB, KCPT, true>(a, sw, nwc, lo, hi, s_ids, cl.K, kw, i % KW_STRIPES, b, dst, stage,
+                                          s_sb, s_hist, s_tstart, s_off, s_w);
+        else
+          kw_scatter_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, s_ids, cl.K, kw, i % KW_STRIPES, b, dst, stage,
+                                           s_sb, s_hist, s_tstart, s_off, s_w);
       }
       fence_proxy_async_smem();   // the next TMA copy reuses the window
       __syncthreads();
@@ -1350,6 +1368,8 @@ template <int KB> cudaError_t seed_impl(const SortArgs &a, cudaStream_t s) {
 template <int KB> cudaError_t partition_impl(const SortArgs &a, cudaStream_t s) {
   if (a.tile_cpt == 4) {
     k_partition<KB, 4><<<partition_grid<KB, 4>(), NT, part_smem(4), s>>>(a);
+  } else if (a.tile_cpt == 16) {
+    k_partition<KB, 16><<<partition_grid<KB, 16>(), NT, part_smem(16), s>>>(a);
   } else {
     k_partition<KB, 8><<<partition_grid<KB, 8>(), NT, part_smem(8), s>>>(a);
   }

@@ -52,13 +52,18 @@ int64_t g_leaf_cutoff = 0;
 int64_t g_seed = 0x22050598;
 int64_t g_spin_limit = 1 << 22;
 int64_t g_test_stall = 0;
-int64_t g_tile_bytes = 0;     // 0: 32 KiB partition tile windows
+int64_t g_tile_bytes = 0;     // 0: by key size (tile_cpt)
 int64_t g_leaf_threads = 0;   // 0: 16 keys per thread at the cutoff
 int64_t g_kway = 1;           // K-way levels for ranges of >= 4 x the leaf cutoff
 
-int tile_cpt() {
+// 16-byte chunks per thread of a partition tile window. Default: 64 KiB
+// windows (3 blocks per SM) for 8- and 16-byte keys, 32 KiB (5 per SM) for
+// narrower keys, whose K-way tiles are capped at 16 keys per thread and so
+// gain nothing from the larger window.
+int tile_cpt(int kb) {
   std::lock_guard<std::mutex> lk(g_mu);
-  return g_tile_bytes == 16384 ? 4 : 8;
+  if (g_tile_bytes == 0) return kb >= 8 ? 16 : 8;
+  return g_tile_bytes == 16384 ? 4 : g_tile_bytes == 65536 ? 16 : 8;
 }
 
 unsigned leaf_cutoff_for(int kb) {
@@ -72,7 +77,7 @@ unsigned leaf_cutoff_for(int kb) {
 // Workspace layout.
 // ---------------------------------------------------------------------------
 struct Layout {
-  size_t hdr, segs, items, lw, lb, fb, kw, alt, total;
+  size_t hdr, segs, items, lw, lb, fb, kw, ids, alt, total;
   unsigned cap_q, cap_segs, cap_lw, cap_lb, cap_fb, cap_kw;
 };
 
@@ -111,6 +116,7 @@ Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_lim
   L.lb = off; off = align256(off + cap_lb * sizeof(LeafEntry));
   L.fb = off; off = align256(off + cap_fb * sizeof(LeafEntry));
   L.kw = off; off = align256(off + cap_kw * sizeof(KwayDesc));
+  L.ids = off; off = align256(off + n + 16);
   L.alt = off;
   if (with_alt) off = align256(off + n * (uint64_t)kb);
   L.total = off;
@@ -245,7 +251,7 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   const int kb = key_bytes(j.dt);
   const unsigned C = leaf_cutoff_for(kb);
   int64_t depth_limit, seed, spin, stall, leaf_threads, kway;
-  const int cpt = j.mode == MODE_SORT ? tile_cpt() : PART_CPT;
+  const int cpt = j.mode == MODE_SORT ? tile_cpt(kb) : PART_CPT;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     depth_limit = g_depth_limit;
@@ -270,6 +276,7 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   a.leaf_block = (LeafEntry *)(w + L.lb);
   a.fb = (LeafEntry *)(w + L.fb);
   a.kw = (kway && j.mode == MODE_SORT) ? (KwayDesc *)(w + L.kw) : nullptr;
+  a.kw_ids = w + L.ids;
   a.cap_kw = L.cap_kw;
   a.offsets = (const unsigned long long *)j.offsets;
   a.n_total = j.n;
@@ -339,7 +346,7 @@ vq_status sort_common(vq_dtype dt, void *keys, uint64_t n, const uint64_t *offse
       std::lock_guard<std::mutex> lk(g_mu);
       dl = g_depth_limit;
     }
-    const Layout L = make_layout(kb, n, offsets ? S : 1, leaf_cutoff_for(kb), dl, true, tile_cpt());
+    const Layout L = make_layout(kb, n, offsets ? S : 1, leaf_cutoff_for(kb), dl, true, tile_cpt(kb));
     if ((st = owned_ws(s, L.total, &ws, &ws_bytes)) != VQ_OK) return st;
   }
   Job j{dt, keys, nullptr, n, offsets, offsets ? S : 1, asc, MODE_SORT, nullptr, nullptr};
@@ -496,6 +503,7 @@ vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out) {
   out->keys_counted = h.keys_counted;
   out->kway_ranges = h.kway_ranges;
   out->guard = h.guard;
+  out->partition_blocks = h.part_grid;
   out->device_status = h.error;
   return VQ_OK;
 }
@@ -532,7 +540,7 @@ vq_status vqsort_set_option(vq_option opt, int64_t value) {
       return VQ_OK;
     case VQ_OPT_TEST_STALL: g_test_stall = value ? 1 : 0; return VQ_OK;
     case VQ_OPT_TILE_BYTES:
-      if (value != 0 && value != 16384 && value != 32768) return VQ_ERR_INVALID;
+      if (value != 0 && value != 16384 && value != 32768 && value != 65536) return VQ_ERR_INVALID;
       g_tile_bytes = value;
       return VQ_OK;
     case VQ_OPT_LEAF_THREADS:

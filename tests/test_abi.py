@@ -99,3 +99,13 @@ def test_networks_zero_one_principle(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout
     assert "sizes 1 5 19 60" in r.stdout and r.stdout.strip().endswith("ok")
+
+
+def test_stats_struct_matches_header():
+    """The binding's vq_stats fields are the header's, in order."""
+    from paper_2205_05982_gb300 import Stats
+    with open(os.path.join(ROOT, "include", "vqsort.h")) as f:
+        text = f.read()
+    body = text[text.index("typedef struct vq_stats {"):text.index("} vq_stats;")]
+    names = re.findall(r"uint64_t\s+(\w+);", body)
+    assert names == [f for f, _ in Stats._fields_]

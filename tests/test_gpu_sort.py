@@ -300,11 +300,12 @@ def test_kway_bucket_counts(vq, oracle_mod, dtype, n):
     assert st["leaf_keys"] + st["equal_keys"] + st["fallback_keys"] == n
 
 
+@pytest.mark.parametrize("tile", (16384, 65536))
 @pytest.mark.parametrize("dtype", ("u16", "u32", "u64", "u128"))
-def test_kway_small_tile_window(vq, oracle_mod, dtype):
-    """16 KiB tile windows: K-way tiles of half the size, a smaller splitter
-    sample."""
-    vq.set_option("tile_bytes", 16384)
+def test_kway_tile_windows(vq, oracle_mod, dtype, tile):
+    """16 KiB tile windows (K-way tiles of half the default size, a smaller
+    splitter sample) and 64 KiB windows (three blocks per SM)."""
+    vq.set_option("tile_bytes", tile)
     try:
         a = make(dtype, 2_000_003, "uniform", seed=3)
         check_sort(vq, oracle_mod, dtype, a, True)
