@@ -49,7 +49,7 @@ def test_tuning_candidates_valid():
         c = batch.candidates(dt)
         assert c
         for x in c:
-            assert x["tile_bytes"] in (16384, 32768)
+            assert x["tile_bytes"] in (16384, 32768, 65536)
             if x["leaf_threads"]:
                 assert 1 <= x["leaf_cutoff"] // x["leaf_threads"] <= 16
             if dt == "u128":
