@@ -160,7 +160,8 @@ vq_status vqsort_partition_noalloc(vq_dtype dt, const void *d_in, void *d_out, s
 
 /* Waits for `stream` and returns the device-side status latched by the
    last sort that used the workspace d_ws (NULL = the library's workspace
-   for this device and stream). */
+   for this device and stream; VQ_OK, and zero statistics below, while no
+   sort has used that one). */
 vq_status vqsort_last_device_status(const void *d_ws, void *stream);
 
 /* Counters of the last sort on a workspace (waits for `stream`). */

@@ -44,7 +44,7 @@ __host__ constexpr int leaf_nt_for(unsigned cutoff, int threads) {
 __host__ constexpr unsigned default_leaf_cutoff(int kb) {
   return kb == 2 ? 16384u : kb == 4 ? 16384u : kb == 8 ? 8192u : 4096u;
 }
-__host__ constexpr unsigned max_leaf_cutoff(int kb) {
+__host__ __device__ constexpr unsigned max_leaf_cutoff(int kb) {
   return kb <= 8 ? 16384u : 4096u;   // 16-byte keys: at most 4 per thread in registers
 }
 __host__ constexpr unsigned code_bytes(int kb) { return kb == 2 ? 4u : (unsigned)kb; }

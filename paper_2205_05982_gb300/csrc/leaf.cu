@@ -102,9 +102,16 @@ __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, u
   __syncthreads();
 }
 
-// NT threads sort one range of up to 16*NT keys, R = P/NT keys per thread
+// Most keys per thread of a block leaf: 16, or fewer when the largest
+// cutoff of the key size needs fewer (16-byte keys: 4096 / NT).
+template <int KB, int NT> __host__ __device__ constexpr int leaf_rmax() {
+  return (int)max_leaf_cutoff(KB) / NT < 16 ? (int)max_leaf_cutoff(KB) / NT : 16;
+}
+
+// NT threads sort one range of up to RMAX*NT keys, R = P/NT keys per thread
 // where P is the range length rounded up to a power of two (>= NT).
 template <int KB, int NT> __global__ void __launch_bounds__(NT, NT <= 512 ? 2 : 1) k_leaf_block(SortArgs a) {
+  constexpr int RMAX = leaf_rmax<KB, NT>();
   using C = typename KT<KB>::Code;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_idx;
@@ -118,7 +125,7 @@ template <int KB, int NT> __global__ void __launch_bounds__(NT, NT <= 512 ? 2 : 
     __syncthreads();
     if (idx >= n) break;
     const LeafEntry le = a.leaf_block[idx];
-    if (le.begin + le.len > a.n_total || le.len > 16u * NT) {   // guard
+    if (le.begin + le.len > a.n_total || le.len > (unsigned)(RMAX * NT)) {   // guard
       if (threadIdx.x == 0) guard_failed(a, GUARD_LEAF);
       continue;
     }
@@ -134,9 +141,9 @@ template <int KB, int NT> __global__ void __launch_bounds__(NT, NT <= 512 ? 2 : 
     }
     if (len <= NT) block_leaf<KB, 1, NT>(a, src, le.begin, len, raw, sx);
     else if (len <= 2 * NT) block_leaf<KB, 2, NT>(a, src, le.begin, len, raw, sx);
-    else if (len <= 4 * NT) block_leaf<KB, 4, NT>(a, src, le.begin, len, raw, sx);
-    else if (len <= 8 * NT) block_leaf<KB, 8, NT>(a, src, le.begin, len, raw, sx);
-    else block_leaf<KB, 16, NT>(a, src, le.begin, len, raw, sx);
+    else if (len <= 4 * NT || RMAX <= 4) block_leaf<KB, (RMAX < 4 ? RMAX : 4), NT>(a, src, le.begin, len, raw, sx);
+    else if (len <= 8 * NT || RMAX <= 8) block_leaf<KB, (RMAX < 8 ? RMAX : 8), NT>(a, src, le.begin, len, raw, sx);
+    else block_leaf<KB, RMAX, NT>(a, src, le.begin, len, raw, sx);
   }
 }
 
@@ -171,8 +178,9 @@ template <int KB> int leaf_warp_grid() {
 template <int KB> cudaError_t leaf_block_impl(const SortArgs &a, cudaStream_t s) {
   const unsigned C = a.leaf_cutoff < 1024 ? 1024 : a.leaf_cutoff;
   const size_t smem = leaf_block_smem(KB, C);
-  if constexpr (KB == 16) {   // cutoff <= 4096: always 256 threads
-    k_leaf_block<KB, 256><<<leaf_block_grid<KB, 256>(smem), 256, smem, s>>>(a);
+  if constexpr (KB == 16) {   // cutoff <= 4096: at most 8 keys per thread at 512 threads
+    if (a.leaf_threads == 256) k_leaf_block<KB, 256><<<leaf_block_grid<KB, 256>(smem), 256, smem, s>>>(a);
+    else k_leaf_block<KB, 512><<<leaf_block_grid<KB, 512>(smem), 512, smem, s>>>(a);
   } else {
     switch (leaf_nt_for(C, a.leaf_threads)) {
       case 1024: k_leaf_block<KB, 1024><<<leaf_block_grid<KB, 1024>(smem), 1024, smem, s>>>(a); break;

@@ -293,7 +293,7 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   a.kw_min_keys = 4 * C;
   a.kw_target = C / 4;
   a.tile_cpt = (unsigned)cpt;
-  a.leaf_threads = kb == 16 ? 0u : (unsigned)leaf_threads;
+  a.leaf_threads = (unsigned)leaf_threads;   // 16-byte keys: 256 or (default) 512
   a.leaf_cutoff = C;
   a.depth_override = (int)depth_limit;
   a.spin_limit = (unsigned)spin;
@@ -363,8 +363,13 @@ std::map<int, HostCtx> g_host;
 
 vq_status read_header(const void *ws, void *stream, Header *h) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (!ws) ws = lookup_ws(s);
-  if (!ws) return VQ_ERR_INVALID;
+  if (!ws) {
+    ws = lookup_ws(s);
+    if (!ws) {   // no sort has used the library's workspace on this stream yet
+      memset(h, 0, sizeof(Header));
+      return VQ_OK;
+    }
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) return VQ_ERR_CUDA;
   if (cudaMemcpy(h, ws, sizeof(Header), cudaMemcpyDeviceToHost) != cudaSuccess) return VQ_ERR_CUDA;
   return VQ_OK;
