@@ -185,6 +185,8 @@ typedef struct vq_stats {
   uint64_t guard;                /* first failed device bounds guard (0: none); a failed guard
                                     skips the access and latches VQ_ERR_INTERNAL */
   uint64_t partition_blocks;     /* thread blocks of the persistent partition kernel */
+  uint64_t leaves_mid;           /* ranges of 513..2048 keys (16-byte keys: ..1024) sorted by
+                                    128-thread blocks */
 } vq_stats;
 vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out);
 

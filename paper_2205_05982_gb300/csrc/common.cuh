@@ -277,7 +277,9 @@ struct Header {
   unsigned long long kway_ranges;  // ranges split K ways (statistics)
   unsigned long long guard;        // first failed bounds guard (GUARD_*), 0 if none
   unsigned long long part_grid;    // blocks of the partition kernel (statistics)
-  unsigned long long pad[2];
+  unsigned long long n_leaf_mid, cur_leaf_mid;   // mid-size leaf list
+  unsigned long long leaves_mid;   // (statistics)
+  unsigned long long pad[7];
 };
 static_assert(sizeof(Header) % 64 == 0, "header size");
 
@@ -369,7 +371,7 @@ struct SortArgs {
   Header *hdr;
   SegDesc *segs;
   unsigned long long *items;
-  LeafEntry *leaf_warp, *leaf_block, *fb;
+  LeafEntry *leaf_warp, *leaf_mid, *leaf_block, *fb;
   KwayDesc *kw;                        // K-way range records (null: K-way levels off)
   unsigned char *kw_ids;               // bucket of each key, written by K-way counting passes
   const unsigned long long *offsets;   // CSR offsets or null (one segment)
@@ -377,7 +379,8 @@ struct SortArgs {
   unsigned long long num_segments;
   unsigned long long *out_left;        // MODE_PARTITION result
   unsigned long long seed;
-  unsigned int cap_q, cap_segs, cap_leaf_warp, cap_leaf_block, cap_fb, cap_kw;
+  unsigned int cap_q, cap_segs, cap_leaf_warp, cap_leaf_mid, cap_leaf_block, cap_fb, cap_kw;
+  unsigned int mid_max;                // leaves of (WARP_LEAF_MAX, mid_max] keys go to the mid list
   unsigned int tile_keys;              // keys per partition tile
   unsigned int kw_tile_keys;           // keys per K-way tile
   unsigned int kw_min_keys;            // smallest range split K ways

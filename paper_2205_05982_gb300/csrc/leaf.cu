@@ -5,6 +5,8 @@
 //   - k_leaf_warp: one warp per range of <= 512 keys; each lane holds R keys
 //     (R = 1..16, the smallest that fits), padded with the all-ones code,
 //     which is the last value in sort order (Sec. 2.3 padding rule).
+//   - k_leaf_mid: 128 threads per range of up to 2048 keys (16-byte keys:
+//     1024), 8 or 16 keys per thread.
 //   - k_leaf_block: cutoff/16 threads per range of up to the cutoff;
 //     cross-warp merge steps exchange registers through shared memory, and
 //     the sorted keys are staged in shared memory for coalesced stores.
@@ -147,6 +149,47 @@ template <int KB, int NT> __global__ void __launch_bounds__(NT, NT <= 512 ? 2 : 
   }
 }
 
+// Mid-size leaves: one MID_NT-thread block per range of (WARP_LEAF_MAX,
+// mid_max_keys(KB)] keys, 8 or 16 keys per thread.
+template <int KB> __global__ void __launch_bounds__(MID_NT, KB == 16 ? 4 : 8) k_leaf_mid(SortArgs a) {
+  using C = typename KT<KB>::Code;
+  constexpr unsigned MAXK = mid_max_keys(KB);
+  __shared__ C sx[MAXK + MAXK / 32];
+  __shared__ unsigned long long s_idx;
+  const unsigned long long n = a.hdr->n_leaf_mid;
+  if (a.hdr->abort) return;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(&a.hdr->cur_leaf_mid, 1ull);
+    __syncthreads();
+    const unsigned long long idx = s_idx;
+    __syncthreads();
+    if (idx >= n) break;
+    const LeafEntry le = a.leaf_mid[idx];
+    if (le.begin + le.len > a.n_total || le.len > MAXK) {   // guard
+      if (threadIdx.x == 0) guard_failed(a, GUARD_LEAF);
+      continue;
+    }
+    const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
+    const bool raw = le.flags & SEG_RAW;
+    const unsigned len = le.len;
+    if (len <= 4 * MID_NT) block_leaf<KB, 4, MID_NT>(a, src, le.begin, len, raw, sx);
+    else if (len <= 8 * MID_NT || KB == 16) block_leaf<KB, 8, MID_NT>(a, src, le.begin, len, raw, sx);
+    else block_leaf<KB, (KB == 16 ? 8 : 16), MID_NT>(a, src, le.begin, len, raw, sx);
+  }
+}
+
+template <int KB> int leaf_mid_grid() {
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_leaf_mid<KB>, MID_NT, 0);
+    grid = sms * (per > 0 ? per : 1);
+  }
+  return grid;
+}
+
 template <int KB, int NT> int leaf_block_grid(size_t smem) {
   static int grid = 0;
   static size_t last = 0;
@@ -191,6 +234,11 @@ template <int KB> cudaError_t leaf_block_impl(const SortArgs &a, cudaStream_t s)
   return cudaGetLastError();
 }
 
+template <int KB> cudaError_t leaf_mid_impl(const SortArgs &a, cudaStream_t s) {
+  k_leaf_mid<KB><<<leaf_mid_grid<KB>(), MID_NT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int KB> cudaError_t leaf_warp_impl(const SortArgs &a, cudaStream_t s) {
   k_leaf_warp<KB><<<leaf_warp_grid<KB>(), 256, 0, s>>>(a);
   return cudaGetLastError();
@@ -204,6 +252,16 @@ cudaError_t launch_leaf_warp(int kb, const SortArgs &a, cudaStream_t s) {
     case 4: return leaf_warp_impl<4>(a, s);
     case 8: return leaf_warp_impl<8>(a, s);
     case 16: return leaf_warp_impl<16>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_leaf_mid(int kb, const SortArgs &a, cudaStream_t s) {
+  switch (kb) {
+    case 2: return leaf_mid_impl<2>(a, s);
+    case 4: return leaf_mid_impl<4>(a, s);
+    case 8: return leaf_mid_impl<8>(a, s);
+    case 16: return leaf_mid_impl<16>(a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -23,7 +23,7 @@ using namespace vq;
 namespace {
 
 constexpr unsigned NOALLOC_TILES = 65536;
-constexpr size_t NOALLOC_HDR = 256;                          // Header (256-byte aligned)
+constexpr size_t NOALLOC_HDR = 512;                          // Header, rounded up to 256 bytes
 constexpr size_t NOALLOC_SEGS = 64 * sizeof(SegDesc);        // the one range (room to spare)
 constexpr size_t NOALLOC_BYTES = NOALLOC_HDR + NOALLOC_SEGS + (size_t)NOALLOC_TILES * 8;
 static_assert(sizeof(Header) <= NOALLOC_HDR, "header does not fit");

@@ -197,14 +197,25 @@ __device__ unsigned long long reserve(const SortArgs &a, unsigned long long *cou
 // A finished range of keys that only needs sorting by a leaf network, or
 // only decoding (all equal), or the merge fallback. Returns the keys handed
 // over (counted off `remaining` by the caller).
+// The leaf list for a range of m keys (at most the cutoff): warp leaves up to
+// WARP_LEAF_MAX keys, mid-size leaves up to a.mid_max, block leaves above.
+struct LeafList {
+  unsigned long long *n, *stat;
+  LeafEntry *list;
+  unsigned cap;
+};
+__device__ __forceinline__ LeafList leaf_list(const SortArgs &a, uint64_t m) {
+  if (m <= WARP_LEAF_MAX) return LeafList{&a.hdr->n_leaf_warp, &a.hdr->leaves_warp, a.leaf_warp, a.cap_leaf_warp};
+  if (m <= a.mid_max) return LeafList{&a.hdr->n_leaf_mid, &a.hdr->leaves_mid, a.leaf_mid, a.cap_leaf_mid};
+  return LeafList{&a.hdr->n_leaf_block, &a.hdr->leaves_block, a.leaf_block, a.cap_leaf_block};
+}
+
 __device__ void emit_leaf(const SortArgs &a, uint64_t b, uint64_t m, unsigned flags, RangeScratch &rs) {
-  const bool warp = m <= WARP_LEAF_MAX;
-  const unsigned long long i = warp ? reserve(a, &a.hdr->n_leaf_warp, a.cap_leaf_warp, 1, rs)
-                                    : reserve(a, &a.hdr->n_leaf_block, a.cap_leaf_block, 1, rs);
+  const LeafList L = leaf_list(a, m);
+  const unsigned long long i = reserve(a, L.n, L.cap, 1, rs);
   if (i != ~0ull && threadIdx.x == 0) {
-    LeafEntry *l = warp ? a.leaf_warp : a.leaf_block;
-    l[i] = LeafEntry{b, (unsigned)m, flags};
-    atomicAdd(warp ? &a.hdr->leaves_warp : &a.hdr->leaves_block, 1ull);
+    L.list[i] = LeafEntry{b, (unsigned)m, flags};
+    atomicAdd(L.stat, 1ull);
     atomicAdd(&a.hdr->leaf_keys, m);
   }
 }
@@ -604,11 +615,11 @@ __device__ void finish_kway_scatter(const SortArgs &a, const SegDesc &sd, unsign
     } else if (ce > cb) {
       const uint64_t mc = ce - cb;
       if (mc <= a.leaf_cutoff) {
-        const bool warp = mc <= WARP_LEAF_MAX;
-        const unsigned long long i = atomicAdd(warp ? &a.hdr->n_leaf_warp : &a.hdr->n_leaf_block, 1ull);
-        if (i < (warp ? a.cap_leaf_warp : a.cap_leaf_block)) {
-          (warp ? a.leaf_warp : a.leaf_block)[i] = LeafEntry{cb, (unsigned)mc, parity};
-          atomicAdd(warp ? &a.hdr->leaves_warp : &a.hdr->leaves_block, 1ull);
+        const LeafList L = leaf_list(a, mc);
+        const unsigned long long i = atomicAdd(L.n, 1ull);
+        if (i < L.cap) {
+          L.list[i] = LeafEntry{cb, (unsigned)mc, parity};
+          atomicAdd(L.stat, 1ull);
           atomicAdd(&a.hdr->leaf_keys, mc);
         } else {
           raise_error(a, ERR_INTERNAL);

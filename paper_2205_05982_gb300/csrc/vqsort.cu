@@ -77,8 +77,8 @@ unsigned leaf_cutoff_for(int kb) {
 // Workspace layout.
 // ---------------------------------------------------------------------------
 struct Layout {
-  size_t hdr, segs, items, lw, lb, fb, kw, ids, alt, total;
-  unsigned cap_q, cap_segs, cap_lw, cap_lb, cap_fb, cap_kw;
+  size_t hdr, segs, items, lw, lm, lb, fb, kw, ids, alt, total;
+  unsigned cap_q, cap_segs, cap_lw, cap_lm, cap_lb, cap_fb, cap_kw;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -100,11 +100,13 @@ Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_lim
   // in two instead
   const uint64_t cap_kw = 2 * (n / (4ull * C) + 1) + 64;
   const uint64_t cap_lw = 2 * cap_segs + S + 16;
+  const uint64_t cap_lm = n / (WARP_LEAF_MAX + 1) + S + 16;   // mid leaves hold > 512 keys each
   const uint64_t cap_lb = n / 512 + n / C + 2 * cap_segs + S + 16;
   const uint64_t cap_fb = n / (C + 1ull) + S + 16;
   L.cap_segs = (unsigned)cap_segs;
   L.cap_q = (unsigned)cap_q;
   L.cap_lw = (unsigned)cap_lw;
+  L.cap_lm = (unsigned)cap_lm;
   L.cap_lb = (unsigned)cap_lb;
   L.cap_fb = (unsigned)cap_fb;
   L.cap_kw = (unsigned)cap_kw;
@@ -113,6 +115,7 @@ Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_lim
   L.segs = off; off = align256(off + cap_segs * sizeof(SegDesc));
   L.items = off; off = align256(off + cap_q * 8);
   L.lw = off; off = align256(off + cap_lw * sizeof(LeafEntry));
+  L.lm = off; off = align256(off + cap_lm * sizeof(LeafEntry));
   L.lb = off; off = align256(off + cap_lb * sizeof(LeafEntry));
   L.fb = off; off = align256(off + cap_fb * sizeof(LeafEntry));
   L.kw = off; off = align256(off + cap_kw * sizeof(KwayDesc));
@@ -273,6 +276,7 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   a.segs = (SegDesc *)(w + L.segs);
   a.items = (unsigned long long *)(w + L.items);
   a.leaf_warp = (LeafEntry *)(w + L.lw);
+  a.leaf_mid = (LeafEntry *)(w + L.lm);
   a.leaf_block = (LeafEntry *)(w + L.lb);
   a.fb = (LeafEntry *)(w + L.fb);
   a.kw = (kway && j.mode == MODE_SORT) ? (KwayDesc *)(w + L.kw) : nullptr;
@@ -286,6 +290,8 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   a.cap_q = L.cap_q;
   a.cap_segs = L.cap_segs;
   a.cap_leaf_warp = L.cap_lw;
+  a.cap_leaf_mid = L.cap_lm;
+  a.mid_max = mid_leaf_limit(kb);
   a.cap_leaf_block = L.cap_lb;
   a.cap_fb = L.cap_fb;
   a.tile_keys = part_tile_keys(kb, cpt);
@@ -316,6 +322,7 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   if ((e = timed("partition", s, [&] { return launch_partition(kb, a, s); })) != cudaSuccess) return cuda_status(e);
   if (j.mode == MODE_SORT) {
     if ((e = timed("leaf_warp", s, [&] { return launch_leaf_warp(kb, a, s); })) != cudaSuccess) return cuda_status(e);
+    if ((e = timed("leaf_mid", s, [&] { return launch_leaf_mid(kb, a, s); })) != cudaSuccess) return cuda_status(e);
     if ((e = timed("leaf_block", s, [&] { return launch_leaf_block(kb, a, s); })) != cudaSuccess) return cuda_status(e);
     if ((e = timed("fallback", s, [&] { return launch_fallback(kb, a, s); })) != cudaSuccess) return cuda_status(e);
   }
@@ -509,6 +516,7 @@ vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out) {
   out->kway_ranges = h.kway_ranges;
   out->guard = h.guard;
   out->partition_blocks = h.part_grid;
+  out->leaves_mid = h.leaves_mid;
   out->device_status = h.error;
   return VQ_OK;
 }
