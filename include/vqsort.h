@@ -187,6 +187,8 @@ typedef struct vq_stats {
   uint64_t partition_blocks;     /* thread blocks of the persistent partition kernel */
   uint64_t leaves_mid;           /* ranges of 513..2048 keys (16-byte keys: ..1024) sorted by
                                     128-thread blocks */
+  uint64_t leaf_ce;              /* compare-exchanges run by the leaf sorting networks
+                                    (padded sizes included) */
 } vq_stats;
 vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out);
 

@@ -44,7 +44,7 @@ class Stats(ctypes.Structure):
         "keys_partitioned", "tiles", "segments", "leaves_warp", "leaves_block", "leaf_keys",
         "equal_ranges", "equal_keys", "degenerate", "fallback_ranges", "fallback_keys",
         "max_depth", "device_status", "keys_counted", "kway_ranges", "guard",
-        "partition_blocks", "leaves_mid")]
+        "partition_blocks", "leaves_mid", "leaf_ce")]
 
 
 _lib = None

@@ -279,7 +279,8 @@ struct Header {
   unsigned long long part_grid;    // blocks of the partition kernel (statistics)
   unsigned long long n_leaf_mid, cur_leaf_mid;   // mid-size leaf list
   unsigned long long leaves_mid;   // (statistics)
-  unsigned long long pad[7];
+  unsigned long long leaf_ce;      // compare-exchanges run by the leaf networks (statistics)
+  unsigned long long pad[6];
 };
 static_assert(sizeof(Header) % 64 == 0, "header size");
 

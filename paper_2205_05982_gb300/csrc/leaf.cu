@@ -28,6 +28,14 @@ template <int KB> __device__ __forceinline__ typename KT<KB>::Code load_key(cons
   }
 }
 
+// Compare-exchanges of the bitonic sorting network on P = G*R keys (G threads
+// of R keys, P a power of two): P/2 per stage, L(L+1)/2 stages, L = log2 P.
+template <int G, int R> __device__ __forceinline__ unsigned long long network_ce() {
+  constexpr unsigned long long P = (unsigned long long)G * R;
+  constexpr unsigned L = ilog2((unsigned)P);
+  return P / 2 * L * (L + 1) / 2;
+}
+
 template <int KB, int R>
 __device__ __forceinline__ void warp_leaf(const SortArgs &a, const void *src, uint64_t b, unsigned len, bool raw,
                                           unsigned lane) {
@@ -49,6 +57,7 @@ __device__ __forceinline__ void warp_leaf(const SortArgs &a, const void *src, ui
     const unsigned i = lane * R + r;
     if (i < len) store_key<KB>(a.keys, b + i, decode<KB>(k[r], a.codec));
   }
+  if (lane == 0) atomicAdd(&a.hdr->leaf_ce, network_ce<32, R>());
 }
 
 template <int KB> __global__ void __launch_bounds__(256) k_leaf_warp(SortArgs a) {
@@ -101,6 +110,7 @@ __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, u
   }
   __syncthreads();
   for (unsigned j = t; j < len; j += NT) store_key<KB>(a.keys, b + j, decode<KB>(sx[j + (j >> 5)], a.codec));
+  if (t == 0) atomicAdd(&a.hdr->leaf_ce, network_ce<NT, R>());
   __syncthreads();
 }
 

@@ -517,6 +517,7 @@ vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out) {
   out->guard = h.guard;
   out->partition_blocks = h.part_grid;
   out->leaves_mid = h.leaves_mid;
+  out->leaf_ce = h.leaf_ce;
   out->device_status = h.error;
   return VQ_OK;
 }
