@@ -288,6 +288,47 @@ def extra_dtypes(vq, torch, peak, n):
     return out
 
 
+def extra_partition_sweep(vq, torch, peak, reps=10):
+    """One Partition (Sec. 2.1) on its own: 2^24 doubles (the paper's
+    partition microbenchmark) and a sweep of sizes and key types. Each call
+    partitions n uniform keys around the key at n/2 into a second buffer.
+    `kernel_gbs` is the algorithmic traffic (2 x key bytes x n) over the
+    partition kernel's own time; `call_gbs` over the whole call (counter
+    reset, pivot setup and partition kernel, back to back)."""
+    res = {}
+    for dt in ("f64", "u64", "f32", "u32", "i16", "u128"):
+        kb = inputs.KEY_BYTES[dt]
+        for lg in (16, 18, 20, 22, 24, 26):
+            n = 1 << lg
+            a = inputs.make(dt, n, "uniform", seed=lg)
+            src = to_device_bits(a, dt, torch)
+            piv = a[n // 2]
+            for _ in range(3):
+                vq.partition(src, piv, dt)
+            torch.cuda.synchronize()
+            vq.profile_reset()
+            vq.profile_enable(True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                vq.partition(src, piv, dt)
+            e1.record()
+            torch.cuda.synchronize()
+            vq.profile_enable(False)
+            prof = vq.profile_read()
+            call_ms = e0.elapsed_time(e1) / reps
+            pk = prof.get("partition", {"ms": float("nan"), "launches": 1})
+            kern_ms = pk["ms"] / max(1, pk["launches"])
+            byts = 2 * kb * n
+            res[f"{dt}:2^{lg}"] = {"kernel_ms": kern_ms, "kernel_gbs": byts / (kern_ms * 1e-3) / 1e9,
+                                   "kernel_frac": byts / (kern_ms * 1e-3) / 1e9 / peak,
+                                   "call_ms": call_ms, "call_gbs": byts / (call_ms * 1e-3) / 1e9}
+            del src
+    torch.cuda.empty_cache()
+    return res
+
+
 def extra_batched(vq, torch, reps=5):
     """16,384 arrays, sizes log-uniform in [16, 65536], uniform u32 keys:
     one autotuned segmented sort replayed as a CUDA graph vs one plain sort
@@ -504,6 +545,7 @@ def run_gpu(args):
             del src
             torch.cuda.empty_cache()
             line["per_dtype"] = extra_dtypes(vq, torch, peak, args.n)
+            line["partition_sweep"] = extra_partition_sweep(vq, torch, peak)
             line["batched"] = extra_batched(vq, torch)
             line["served"] = extra_served(vq, torch, args.served_requests)
         line["cpu_baseline"] = None if args.no_cpu else cpu_baseline(args, a, args.cpu_seconds)

@@ -138,7 +138,7 @@ vq_status vqsort_choose_pivot(vq_dtype dt, const void *d_keys, size_t n, uint64_
    and can fail once a fixed memory budget is used up (a latency-bound
    serving loop, code running inside another allocator's hooks).
    Its scratch (counters, the range descriptor and the tile queue) is a
-   fixed array of about 513 KiB in device memory that belongs to the loaded
+   fixed array of about 517 KiB in device memory that belongs to the loaded
    library: every GPU that loads libvqsort.so holds it until the process
    exits. Limit: n <= 65536 * ((32768 - 16) / key bytes) keys (about 1.07e9
    2-byte, 5.4e8 4-byte, 2.7e8 8-byte, 1.3e8 16-byte keys); larger n returns

@@ -254,7 +254,7 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   const int kb = key_bytes(j.dt);
   const unsigned C = leaf_cutoff_for(kb);
   int64_t depth_limit, seed, spin, stall, leaf_threads, kway;
-  const int cpt = j.mode == MODE_SORT ? tile_cpt(kb) : PART_CPT;
+  const int cpt = tile_cpt(kb);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     depth_limit = g_depth_limit;
@@ -466,7 +466,7 @@ vq_status vqsort_partition(vq_dtype dt, const void *d_in, void *d_out, size_t n,
   if ((st = check_device()) != VQ_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const int kb = key_bytes(dt);
-  const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb), -1, false, PART_CPT);
+  const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb), -1, false, tile_cpt(kb));
   void *ws;
   size_t wsb;
   if ((st = owned_ws(s, L.total, &ws, &wsb)) != VQ_OK) return st;

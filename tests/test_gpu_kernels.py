@@ -47,3 +47,30 @@ def test_choose_pivot_matches_oracle(vq, oracle_mod, dtype, offset_keys, ascendi
     want = oracle_mod.choose_pivot(a[offset_keys:offset_keys + n], dtype, addr_mod64, seed, ascending)
     g = got.cpu().numpy().view(a.dtype).reshape(-1)
     assert g.tobytes() == np.asarray(want).tobytes()
+
+
+@pytest.mark.parametrize("dtype", ("f64", "u64", "f32", "u32", "i16", "u128"))
+@pytest.mark.parametrize("lg", (16, 20, 24))
+def test_partition_microbenchmark_sizes(vq, oracle_mod, dtype, lg):
+    """The partition-only microbenchmark's workloads (one Partition of 2^lg
+    uniform keys around the key at n/2; the paper times 2^24 doubles):
+    left count exact, each side equal to the oracle's as a multiset."""
+    n = 1 << lg
+    a = inputs.make(dtype, n, "uniform", seed=lg)
+    piv = a[n // 2]
+    want, wl = oracle_mod.partition(a, piv, dtype, True)
+    out, left = vq.partition(to_dev(a, dtype), piv, dtype)
+    got = to_host(out, dtype, a)
+    L = int(left.item())
+    assert L == wl
+    w = 16 if inputs.KEY_BYTES[dtype] == 16 else inputs.KEY_BYTES[dtype]
+    view = {2: np.uint16, 4: np.uint32, 8: np.uint64, 16: np.uint64}[w]
+
+    def rows(x):
+        v = np.ascontiguousarray(x).view(view)
+        if w == 16:
+            v = v.reshape(-1, 2)
+            return v[np.lexsort((v[:, 0], v[:, 1]))]
+        return np.sort(v)
+    assert np.array_equal(rows(got[:L]), rows(want[:L]))
+    assert np.array_equal(rows(got[L:]), rows(want[L:]))
