@@ -134,6 +134,20 @@ def decode(codes: np.ndarray, dtype: str, ascending: bool = True) -> np.ndarray:
     return out
 
 
+def sort_stable(keys: np.ndarray, dtype: str, ascending: bool = True):
+    """Stable sort (Sec. 5: a unique row id appended below the key makes
+    Quicksort stable). Returns (sorted keys, rows): rows[i] is the input
+    position of output key i, and keys whose codes are equal keep their input
+    order. By definition: order the rows by (code, row); numpy's lexsort is
+    the library sort used as that step. 2-, 4- and 8-byte key types."""
+    if KEY_BYTES[dtype] == 16:
+        raise ValueError("stable sort covers 2-, 4- and 8-byte keys")
+    a = _keys(keys, dtype)
+    codes = encode(a, dtype, ascending)
+    rows = np.lexsort((np.arange(codes.shape[0], dtype=np.uint64), codes)).astype(np.uint64)
+    return a[rows], rows
+
+
 def partition(keys: np.ndarray, pivot, dtype: str, ascending: bool = True):
     """Stable partition by definition: (out, left_count)."""
     a = _keys(keys, dtype)

@@ -326,3 +326,26 @@ def test_choose_pivot_rule(oracle_mod, dtype, addr_mod64, ascending):
     rows.sort(key=k, reverse=not ascending)
     got = oracle_mod.choose_pivot(a, dtype, addr_mod64, seed, ascending)
     assert np.asarray(got).tobytes() == rows[127].tobytes()
+
+
+@pytest.mark.parametrize("dtype", ("i16", "u32", "f32", "i64", "f64"))
+@pytest.mark.parametrize("ascending", (True, False))
+def test_sort_stable_matches_python_stable_sort(oracle_mod, dtype, ascending):
+    """Pinned to Python's own stable sort (a merge sort, no code shared):
+    rows in output order, keys by the total order, ties in input order."""
+    rng = np.random.default_rng(11)
+    a = inputs.make(dtype, 400, "distinct16", seed=5, specials=dtype.startswith("f"))
+    a = a[rng.permutation(a.shape[0])]
+    keys, rows = oracle_mod.sort_stable(a, dtype, ascending)
+    codes = [int(c) for c in oracle_mod.encode(a, dtype, ascending)]
+    want = sorted(range(len(codes)), key=lambda i: codes[i])   # stable by the language
+    assert [int(r) for r in rows] == want
+    assert np.ascontiguousarray(keys).tobytes() == np.ascontiguousarray(a[want]).tobytes()
+
+
+def test_sort_stable_ties_keep_input_order(oracle_mod):
+    """All-equal keys: the permutation is the identity, ascending or not."""
+    a = np.full(17, 5, dtype=np.uint32)
+    for asc in (True, False):
+        _, rows = oracle_mod.sort_stable(a, "u32", asc)
+        assert rows.tolist() == list(range(17))
