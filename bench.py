@@ -288,6 +288,35 @@ def extra_dtypes(vq, torch, peak, n):
     return out
 
 
+def extra_stable(vq, torch, n, reps=5):
+    """Stable sorts (Sec. 5 row-id recipe) of n uniform keys: keys of up to 4
+    bytes travel as 64-bit (code, row) codes, 8-byte keys as 128-bit ones."""
+    res = {}
+    for dt in ("u32", "u64"):
+        a = inputs.make(dt, n, "uniform")
+        src = to_device_bits(a, dt, torch)
+        t = src.clone()
+        for _ in range(2):
+            t.copy_(src)
+            vq.sort_stable_(t, dt)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            t.copy_(src)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            vq.sort_stable_(t, dt)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        m = float(np.median(ms))
+        res[dt] = {"gkeys_per_s": n / (m * 1e-3) / 1e9, "ms": m}
+        del src, t
+        torch.cuda.empty_cache()
+    return res
+
+
 def extra_partition_sweep(vq, torch, peak, reps=10):
     """One Partition (Sec. 2.1) on its own: 2^24 doubles (the paper's
     partition microbenchmark) and a sweep of sizes and key types. Each call
@@ -546,6 +575,7 @@ def run_gpu(args):
             torch.cuda.empty_cache()
             line["per_dtype"] = extra_dtypes(vq, torch, peak, args.n)
             line["partition_sweep"] = extra_partition_sweep(vq, torch, peak)
+            line["stable"] = extra_stable(vq, torch, args.n)
             line["batched"] = extra_batched(vq, torch)
             line["served"] = extra_served(vq, torch, args.served_requests)
         line["cpu_baseline"] = None if args.no_cpu else cpu_baseline(args, a, args.cpu_seconds)

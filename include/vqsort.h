@@ -77,6 +77,18 @@ vq_status vqsort_sort(vq_dtype dt, void *d_keys, size_t n, int ascending, void *
    vqsort_sort(VQ_KV64, ...). */
 vq_status vqsort_sort_kv(void *d_pairs, size_t n, int ascending, void *stream);
 
+/* Stable sort (Sec. 5: appending a unique row identifier below the key makes
+   Quicksort stable). Sorts the n keys at d_keys in place, in the same order
+   as vqsort_sort, and writes to d_rows (device, n uint64_t, 8-byte aligned)
+   the input position of each output key; keys that compare equal (same bit
+   pattern after encoding) keep their input order, in both sort orders.
+   2-, 4- and 8-byte key types; 16-byte types return VQ_ERR_UNSUPPORTED.
+   Each key's code is packed with its row (keys of up to 4 bytes into a
+   64-bit code, 8-byte keys into a 128-bit one), the packed codes are sorted
+   and unpacked; the library's workspace for this stream grows to hold them. */
+vq_status vqsort_sort_stable(vq_dtype dt, void *d_keys, size_t n, int ascending, uint64_t *d_rows,
+                             void *stream);
+
 /* Sorts num_segments independent arrays in one set of launches: segment s
    is keys [d_offsets[s], d_offsets[s+1]) of d_keys (CSR, uint64, device
    memory, num_segments + 1 entries, non-decreasing, last entry == n_total).

@@ -74,6 +74,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     sigs = {
         "vqsort_sort": ([i32, vp, sz, i32, vp], i32),
         "vqsort_sort_kv": ([vp, sz, i32, vp], i32),
+        "vqsort_sort_stable": ([i32, vp, sz, i32, vp, vp], i32),
         "vqsort_sort_segmented": ([i32, vp, sz, vp, sz, i32, vp], i32),
         "vqsort_workspace_bytes": ([i32, sz, sz], sz),
         "vqsort_sort_ws": ([i32, vp, sz, i32, vp, sz, vp], i32),
@@ -169,6 +170,17 @@ def sort_kv_(pairs, descending: bool = False, stream=None):
     _check(load().vqsort_sort_kv(ctypes.c_void_p(pairs.data_ptr()), n, int(not descending),
                                  _stream(stream)), "vqsort_sort_kv")
     return pairs
+
+
+def sort_stable_(t, dtype: str | None = None, descending: bool = False, stream=None):
+    """Stable in-place sort (Sec. 5 row-id recipe); returns the int64 tensor
+    of input positions of the output keys (equal keys keep input order)."""
+    torch = _torch()
+    dtype, n = _prep(t, dtype)
+    rows = torch.empty(n, dtype=torch.int64, device=t.device)
+    _check(load().vqsort_sort_stable(CODE[dtype], ctypes.c_void_p(t.data_ptr()), n, int(not descending),
+                                     ctypes.c_void_p(rows.data_ptr()), _stream(stream)), "vqsort_sort_stable")
+    return rows
 
 
 def _offsets(offsets, device):

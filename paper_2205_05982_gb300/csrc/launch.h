@@ -70,5 +70,8 @@ cudaError_t launch_leaf_warp(int kb, const SortArgs &a, cudaStream_t s);
 cudaError_t launch_leaf_mid(int kb, const SortArgs &a, cudaStream_t s);
 cudaError_t launch_leaf_block(int kb, const SortArgs &a, cudaStream_t s);
 cudaError_t launch_fallback(int kb, const SortArgs &a, cudaStream_t s);
+cudaError_t launch_stable_pack(int kb, const void *keys, void *packed, uint64_t n, Codec cd, cudaStream_t s);
+cudaError_t launch_stable_unpack(int kb, const void *packed, void *keys, uint64_t *rows, uint64_t n, Codec cd,
+                                 cudaStream_t s);
 
 }  // namespace vq

@@ -474,6 +474,45 @@ vq_status vqsort_partition(vq_dtype dt, const void *d_in, void *d_out, size_t n,
   return run(j, ws, wsb, s);
 }
 
+vq_status vqsort_sort_stable(vq_dtype dt, void *d_keys, size_t n, int ascending, uint64_t *d_rows,
+                             void *stream) {
+  vq_status st = check_keys(dt, d_keys, n);
+  if (st != VQ_OK) return st;
+  const int kb = key_bytes(dt);
+  if (kb == 16) return VQ_ERR_UNSUPPORTED;
+  if (n > 0 && (!d_rows || ((uintptr_t)d_rows & 7))) return VQ_ERR_INVALID;
+  if (n == 0) return VQ_OK;
+  if ((st = check_device()) != VQ_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // packed codes: 8 bytes for keys of up to 4 bytes, 16 for 8-byte keys
+  const vq_dtype pdt = kb == 8 ? VQ_U128 : VQ_U64;
+  const int pkb = key_bytes(pdt);
+  int64_t dl;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    dl = g_depth_limit;
+  }
+  const Layout L = make_layout(pkb, n, 1, leaf_cutoff_for(pkb), dl, true, tile_cpt(pkb));
+  const size_t packed_off = align256(L.total);
+  void *ws;
+  size_t wsb;
+  if ((st = owned_ws(s, packed_off + (size_t)n * pkb, &ws, &wsb)) != VQ_OK) return st;
+  void *packed = (unsigned char *)ws + packed_off;
+  const Codec cd = codec_of(dt, ascending);
+  cudaError_t e;
+  if ((e = timed("stable_pack", s, [&] { return launch_stable_pack(kb, d_keys, packed, n, cd, s); })) !=
+      cudaSuccess)
+    return cuda_status(e);
+  if (n > 1) {
+    Job j{pdt, packed, nullptr, n, nullptr, 1, 1, MODE_SORT, nullptr, nullptr};
+    if ((st = run(j, ws, packed_off, s)) != VQ_OK) return st;
+  }
+  if ((e = timed("stable_unpack", s, [&] { return launch_stable_unpack(kb, packed, d_keys, d_rows, n, cd, s); })) !=
+      cudaSuccess)
+    return cuda_status(e);
+  return VQ_OK;
+}
+
 vq_status vqsort_choose_pivot(vq_dtype dt, const void *d_keys, size_t n, uint64_t seed, int ascending,
                               void *d_pivot_out, void *stream) {
   vq_status st = check_keys(dt, d_keys, n);
