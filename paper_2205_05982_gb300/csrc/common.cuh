@@ -303,7 +303,7 @@ enum : unsigned int {
   SEG_PARITY = 1u,   // keys live in the alternate buffer (else the user buffer)
   SEG_RAW = 2u,      // keys are still in input form (root ranges)
   SEG_EXCL = 4u,     // pivot is one below a repeated maximum: right side all equal
-  SEG_KWAY = 16u,    // split 2^piv_hi ways by the splitters of K-way record piv_lo
+  SEG_KWAY = 16u,    // split into piv_hi buckets by the splitters of K-way record piv_lo
   SEG_NOKWAY = 32u,  // a K-way split made no progress here: split in two
 };
 
@@ -338,8 +338,8 @@ constexpr unsigned KW_STRIPES = 16;
 constexpr unsigned KW_TABLE_BITS = 10;
 constexpr unsigned KW_TABLE = 1u << KW_TABLE_BITS;
 
-// Splitters and per-bucket counters of one K-way range (K = 2^kbits buckets,
-// kbits kept in the range descriptor's piv_hi).
+// Splitters and per-bucket counters of one K-way range (the bucket count is
+// kept in the range descriptor's piv_hi).
 struct KwayDesc {
   // counting pass: keys of stripe s in bucket b (atomic); then, for the
   // scatter pass, the next free slot of stripe s in bucket b, relative to the
@@ -351,7 +351,11 @@ struct KwayDesc {
   // per value p of the table bits: (number of splitters whose table bits
   // are below p) | (number equal to p) << 8
   unsigned short table[KW_TABLE];
-  unsigned int shift;                    // leading bits shared by splitters 1 and K-1
+  unsigned int shift;                    // leading bits shared by the first and last splitter
+  unsigned int nsplit;                   // splitters (K - 1, or the distinct values in
+                                         // equality mode)
+  unsigned int eqmode;                   // equality mode: 2 * nsplit + 1 buckets, the odd
+                                         // ones holding the keys equal to one splitter
   unsigned int pad;
 };
 

@@ -258,6 +258,30 @@ __device__ void emit_fallback(const SortArgs &a, uint64_t b, uint64_t m, unsigne
 // share its table bits, which are then compared.
 // ---------------------------------------------------------------------------
 
+// Exclusive scan of one value per thread over the block; `total` gets the sum.
+__device__ unsigned long long block_excl_scan(unsigned long long x, unsigned long long *s_w,
+                                              unsigned long long &total) {
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= (unsigned)o) incl += y;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  unsigned long long pre = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < NWARP; ++w) {
+    const unsigned long long v = s_w[w];
+    if (w < (int)warp) pre += v;
+    tot += v;
+  }
+  __syncthreads();
+  total = tot;
+  return pre + incl - x;
+}
+
 // Keys per thread of the splitter sample: as many as the scratch holds.
 template <int KB, int CPT> __host__ __device__ constexpr unsigned kw_sample_r() {
   return KB == 16 ? (CPT >= 8 ? 4u : 2u) : (CPT >= 8 ? 8u : 4u);
@@ -310,14 +334,19 @@ __device__ __forceinline__ unsigned classify(const C &k, const C *split, const u
   return b;
 }
 
-// The bucket lookup of one K-way range, staged in shared memory.
+// The bucket lookup of one K-way range, staged in shared memory: nsp
+// splitters split[1..nsp]; in equality mode (eqb) bucket 2b holds the keys
+// strictly between splitters b and b+1 and bucket 2b+1 the keys equal to
+// splitter b+1.
 template <class C> struct KwLookup {
   const C *split;
   const unsigned short *table;
   C s1, sk;
-  unsigned sh, K;
+  unsigned sh, nsp, eqb;
   __device__ __forceinline__ unsigned operator()(const C &k) const {
-    return classify(k, split, table, s1, sk, sh, K);
+    const unsigned b = classify(k, split, table, s1, sk, sh, nsp + 1);
+    if (!eqb) return b;
+    return 2 * b + ((b < nsp && eq(k, split[b + 1])) ? 1u : 0u);
   }
 };
 
@@ -329,20 +358,25 @@ __device__ __forceinline__ unsigned kway_bits(const SortArgs &a, uint64_t m) {
 }
 
 // Samples R*NT keys of [b, b+m) (64-byte chunks drawn as in sample_pivot),
-// sorts them with the block network and writes splitter i = sample rank
-// i*S/K - 1 (i = 1..K-1) and the lookup table to `kw`. Returns false,
-// writing nothing, when every sampled code is the same (such ranges are
-// split in two).
+// sorts them with the block network and takes splitter i = sample rank
+// i*S/K - 1 (i = 1..K-1). When those repeat a value (heavy duplicates) and
+// the distinct values d number at most 127, the range switches to equality
+// mode: the d distinct values split it into 2d + 1 buckets, every second one
+// holding the keys equal to one splitter, which need no further sorting (the
+// K-way form of a three-way partition). Writes the splitters and the lookup
+// table to `kw` and returns the bucket count, or 0, writing nothing, when
+// every sampled code is the same (such ranges are split in two).
 template <int KB, unsigned R>
-__device__ bool build_splitters(const void *buf, uint64_t b, uint64_t m, bool raw, Codec cd, uint64_t seed,
-                                unsigned kbits, KwayDesc &kw, void *scratch) {
+__device__ unsigned build_splitters(const void *buf, uint64_t b, uint64_t m, bool raw, Codec cd, uint64_t seed,
+                                    unsigned kbits, KwayDesc &kw, void *scratch) {
   using C = typename KT<KB>::Code;
   constexpr unsigned S = R * NT, kc = 64 / KB, ns = S / kc;
-  static_assert(S >= KW_MAX, "at least one sample per bucket");
+  static_assert(S >= 2 * KW_MAX, "sample holds the splitters and their distinct values");
   constexpr unsigned WIDTH = 8 * sizeof(C);
   C *sx = (C *)scratch;
   unsigned long long *s_chunk = (unsigned long long *)(sx + S);
   __shared__ int s_same;
+  __shared__ unsigned long long s_wb[NWARP];
   const uintptr_t addr = (uintptr_t)buf + b * KB;
   const uint64_t off = ((64 - (addr & 63)) & 63) / KB;
   const uint64_t nc = (m - off) / kc;
@@ -365,58 +399,73 @@ __device__ bool build_splitters(const void *buf, uint64_t b, uint64_t m, bool ra
   if (threadIdx.x == NT - 1) s_same = eq(sx[0], k[R - 1]);
   __syncthreads();
   const bool same = s_same;
-  if (same) return false;   // uniform across the block
+  if (same) return 0;   // uniform across the block
   const unsigned K = 1u << kbits, step = S >> kbits;
   C *sp = sx;   // splitters 1..K-1
 #pragma unroll
   for (unsigned r = 0; r < R; ++r) {
     const unsigned rank1 = R * threadIdx.x + r + 1;
     const unsigned i = rank1 / step;
-    if (rank1 % step == 0 && i < K) {
-      sp[i] = k[r];
-      uint64_t lo, hi;
-      code_words<KB>(k[r], lo, hi);
-      kw.split_lo[i] = lo;
-      kw.split_hi[i] = hi;
-    }
+    if (rank1 % step == 0 && i < K) sp[i] = k[r];
   }
   __syncthreads();
-  const unsigned sh = common_prefix(sp[1], sp[K - 1]);
-  if (threadIdx.x == 0) kw.shift = sh;
-  // table[p]: splitters (1..K-1, all sharing the prefix, so their table bits
-  // ascend with i) whose table bits are below p, and how many equal p
+  // distinct splitter values, compacted to dv[1..nd]
+  const unsigned i = threadIdx.x + 1;
+  const bool first = i < K && (i == 1 || !eq(sp[i], sp[i - 1]));
+  unsigned long long nd;
+  const unsigned long long pos = block_excl_scan(first ? 1ull : 0ull, s_wb, nd);
+  const bool eqm = nd < K - 1 && 2 * nd + 1 <= KW_MAX;
+  C *dv = sx + KW_MAX;
+  if (eqm && first) dv[pos + 1] = sp[i];
+  __syncthreads();
+  const C *use = eqm ? dv : sp;
+  const unsigned nsp = eqm ? (unsigned)nd : K - 1;
+  for (unsigned j = threadIdx.x + 1; j <= nsp; j += NT) {
+    uint64_t lo, hi;
+    code_words<KB>(use[j], lo, hi);
+    kw.split_lo[j] = lo;
+    kw.split_hi[j] = hi;
+  }
+  const unsigned sh = common_prefix(use[1], use[nsp]);
+  if (threadIdx.x == 0) {
+    kw.shift = sh;
+    kw.nsplit = nsp;
+    kw.eqmode = eqm;
+  }
+  // table[p]: splitters (all sharing the prefix, so their table bits ascend
+  // with the index) whose table bits are below p, and how many equal p
   for (unsigned p = threadIdx.x; p < KW_TABLE; p += NT) {
     unsigned below = 0, upto = 0;
     if (sh < WIDTH) {
-      unsigned lo = 1, n = K - 1;   // first i with bits(sp[i]) >= p
+      unsigned lo = 1, n = nsp;   // first j with bits(use[j]) >= p
       while (n) {
         const unsigned h = n >> 1;
-        if (table_bits(sp[lo + h], sh) < p) { lo += h + 1; n -= h + 1; } else n = h;
+        if (table_bits(use[lo + h], sh) < p) { lo += h + 1; n -= h + 1; } else n = h;
       }
       below = lo - 1;
-      unsigned lo2 = lo, n2 = K - lo;   // first i with bits(sp[i]) > p
+      unsigned lo2 = lo, n2 = nsp + 1 - lo;   // first j with bits(use[j]) > p
       while (n2) {
         const unsigned h = n2 >> 1;
-        if (table_bits(sp[lo2 + h], sh) <= p) { lo2 += h + 1; n2 -= h + 1; } else n2 = h;
+        if (table_bits(use[lo2 + h], sh) <= p) { lo2 += h + 1; n2 -= h + 1; } else n2 = h;
       }
       upto = lo2 - 1;
     }
     kw.table[p] = (unsigned short)(below | ((upto - below) << 8));
   }
   __syncthreads();
-  return true;
+  return eqm ? 2 * (unsigned)nd + 1 : K;
 }
 
 // Creates a K-way range on record `kid` (splitters already written) and
 // publishes its counting-pass tiles.
 __device__ void make_kway_segment(const SortArgs &a, uint64_t b, uint64_t e, unsigned depth, unsigned flags,
-                                  unsigned depth_limit, unsigned long long kid, unsigned kbits,
+                                  unsigned depth_limit, unsigned long long kid, unsigned K,
                                   RangeScratch &rs) {
   const unsigned T = a.kw_tile_keys;
   const uint64_t m = e - b;
   const unsigned nt = (unsigned)((m + T - 1) / T);
   KwayDesc &kw = a.kw[kid];
-  for (unsigned j = threadIdx.x; j < (1u << kbits); j += NT)
+  for (unsigned j = threadIdx.x; j < K; j += NT)
 #pragma unroll
     for (unsigned st = 0; st < KW_STRIPES; ++st) kw.cnt[st][j] = 0;
   if (threadIdx.x == 0) {
@@ -428,7 +477,7 @@ __device__ void make_kway_segment(const SortArgs &a, uint64_t b, uint64_t e, uns
       d.begin = b;
       d.end = e;
       d.piv_lo = kid;
-      d.piv_hi = kbits;
+      d.piv_hi = K;
       d.cursor = 0;
       d.depth = depth;
       d.flags = flags | SEG_KWAY;
@@ -469,9 +518,9 @@ __device__ void start_range(const SortArgs &a, uint64_t b, uint64_t e, unsigned 
     const unsigned long long kid = rs.idx;
     __syncthreads();
     if (kid != ~0ull) {
-      const unsigned kbits = kway_bits(a, m);
-      if (build_splitters<KB, R>(buf, b, m, raw, a.codec, seed, kbits, a.kw[kid], scratch)) {
-        make_kway_segment(a, b, e, depth, flags, depth_limit, kid, kbits, rs);
+      const unsigned K = build_splitters<KB, R>(buf, b, m, raw, a.codec, seed, kway_bits(a, m), a.kw[kid], scratch);
+      if (K) {
+        make_kway_segment(a, b, e, depth, flags, depth_limit, kid, K, rs);
         return;
       }
     }
@@ -522,37 +571,13 @@ __device__ uint64_t child_range(const SortArgs &a, uint64_t b, uint64_t e, unsig
   return 0;
 }
 
-// Exclusive scan of one value per thread over the block; `total` gets the sum.
-__device__ unsigned long long block_excl_scan(unsigned long long x, unsigned long long *s_w,
-                                              unsigned long long &total) {
-  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long incl = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long y = __shfl_up_sync(FULL, incl, o);
-    if (lane >= (unsigned)o) incl += y;
-  }
-  if (lane == 31) s_w[warp] = incl;
-  __syncthreads();
-  unsigned long long pre = 0, tot = 0;
-#pragma unroll
-  for (int w = 0; w < NWARP; ++w) {
-    const unsigned long long v = s_w[w];
-    if (w < (int)warp) pre += v;
-    tot += v;
-  }
-  __syncthreads();
-  total = tot;
-  return pre + incl - x;
-}
-
 // After the counting pass of a K-way range: bucket bounds from the counts,
 // each stripe's write cursor at its share of the bucket, then the
 // scatter-pass tiles.
 __device__ void finish_kway_count(const SortArgs &a, const SegDesc &sd, unsigned sid, RangeScratch &rs,
                                   unsigned long long *s_w) {
   KwayDesc &kw = a.kw[sd.piv_lo];
-  const unsigned K = 1u << sd.piv_hi;
+  const unsigned K = (unsigned)sd.piv_hi;
   const unsigned tid = threadIdx.x;
   unsigned c[KW_STRIPES];
   unsigned long long cnt = 0;
@@ -594,7 +619,8 @@ __device__ void finish_kway_scatter(const SortArgs &a, const SegDesc &sd, unsign
                                     unsigned long long *s_w) {
   if (a.test_stall && sid == 0) return;   // test hook: children never appear
   const KwayDesc &kw = a.kw[sd.piv_lo];
-  const unsigned K = 1u << sd.piv_hi;
+  const unsigned K = (unsigned)sd.piv_hi;
+  const bool eqm = __ldcg(&kw.eqmode) != 0;
   const unsigned tid = threadIdx.x;
   const unsigned parity = (sd.flags & SEG_PARITY) ^ 1u;
   const unsigned d1 = sd.depth + 1;
@@ -614,7 +640,24 @@ __device__ void finish_kway_scatter(const SortArgs &a, const SegDesc &sd, unsign
       guard_failed(a, GUARD_BOUNDS);
     } else if (ce > cb) {
       const uint64_t mc = ce - cb;
-      if (mc <= a.leaf_cutoff) {
+      if (eqm && (tid & 1)) {
+        // keys equal to one splitter: only decoded and copied, in pieces of
+        // at most the cutoff
+        const unsigned C = a.leaf_cutoff;
+        const unsigned ne = (unsigned)((mc + C - 1) / C);
+        const unsigned long long i0 = atomicAdd(&a.hdr->n_leaf_block, (unsigned long long)ne);
+        if (i0 + ne <= a.cap_leaf_block) {
+          for (unsigned q = 0; q < ne; ++q) {
+            const uint64_t pb = cb + (uint64_t)q * C;
+            a.leaf_block[i0 + q] = LeafEntry{pb, (unsigned)min((uint64_t)C, ce - pb), parity | LEAF_COPY};
+          }
+          atomicAdd(&a.hdr->equal_ranges, 1ull);
+          atomicAdd(&a.hdr->equal_keys, mc);
+        } else {
+          raise_error(a, ERR_INTERNAL);
+        }
+        handed = mc;
+      } else if (mc <= a.leaf_cutoff) {
         const LeafList L = leaf_list(a, mc);
         const unsigned long long i = atomicAdd(L.n, 1ull);
         if (i < L.cap) {
@@ -1125,7 +1168,7 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
   __shared__ unsigned s_off[KW_MAX];
   __shared__ unsigned long long s_w[NWARP];
   __shared__ unsigned char s_sb[TKW];
-  __shared__ unsigned s_shift;
+  __shared__ unsigned s_shift, s_nsp, s_eqm;
   C *s_split = (C *)s_aux;
   unsigned short *s_table = (unsigned short *)(s_aux + KW_MAX * sizeof(C));
   M *stage = (M *)(smem + part_window(CPT) / 2);
@@ -1208,7 +1251,11 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
         s_split[j] = code_of<KB>(__ldcg(&kw.split_lo[j]), KB == 16 ? __ldcg(&kw.split_hi[j]) : 0ull);
       for (unsigned j = tid; j < KW_TABLE / 2; j += NT)
         ((unsigned *)s_table)[j] = __ldcg((const unsigned *)kw.table + j);
-      if (tid == 0) s_shift = __ldcg(&kw.shift);
+      if (tid == 0) {
+        s_shift = __ldcg(&kw.shift);
+        s_nsp = __ldcg(&kw.nsplit);
+        s_eqm = __ldcg(&kw.eqmode);
+      }
       __syncthreads();
     }
     {
@@ -1242,19 +1289,20 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
 
     if (kway) {
       KwayDesc &kw = a.kw[sg.piv_lo];
-      const unsigned kbits = (unsigned)sg.piv_hi;
+      const unsigned K = (unsigned)sg.piv_hi;   // buckets
       KwLookup<C> cl;
       cl.split = s_split;
       cl.table = s_table;
-      cl.K = 1u << kbits;
+      cl.nsp = s_nsp;
+      cl.eqb = s_eqm;
       cl.s1 = s_split[1];
-      cl.sk = s_split[cl.K - 1];
+      cl.sk = s_split[s_nsp];
       cl.sh = s_shift;
       if (!phase1) {
         if (raw) kw_count_tile<KB, KCPT, true>(a, sw, nwc, lo, hi, cl, s_hist, a.kw_ids + t0);
         else kw_count_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, cl, s_hist, a.kw_ids + t0);
         __syncthreads();
-        if (tid < (1u << kbits)) {
+        if (tid < K) {
           const unsigned x = s_hist[tid];
           if (x) atomicAdd(&kw.cnt[i % KW_STRIPES][tid], x);
           s_hist[tid] = 0;
@@ -1263,10 +1311,10 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
         const unsigned char *s_ids =
             (const unsigned char *)stage + ((uintptr_t)(a.kw_ids + t0) & 15);   // copied with the keys
         if (raw)
-          kw_scatter_tile<KB, KCPT, true>(a, sw, nwc, lo, hi, s_ids, cl.K, kw, i % KW_STRIPES, b, dst, stage,
+          kw_scatter_tile<KB, KCPT, true>(a, sw, nwc, lo, hi, s_ids, K, kw, i % KW_STRIPES, b, dst, stage,
                                           s_sb, s_hist, s_tstart, s_off, s_w);
         else
-          kw_scatter_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, s_ids, cl.K, kw, i % KW_STRIPES, b, dst, stage,
+          kw_scatter_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, s_ids, K, kw, i % KW_STRIPES, b, dst, stage,
                                            s_sb, s_hist, s_tstart, s_off, s_w);
       }
       fence_proxy_async_smem();   // the next TMA copy reuses the window

@@ -331,3 +331,31 @@ def test_segmented_with_kway_roots(vq, oracle_mod, dtype):
     st = vq.stats()
     assert st["guard"] == 0 and st["kway_ranges"] >= 1
     assert same_bits(got, want), first_mismatch(got, want)
+
+
+@pytest.mark.parametrize("dtype", ("u64", "i16", "f32", "u128"))
+def test_kway_equality_buckets_16_distinct(vq, oracle_mod, dtype):
+    """16 distinct values: the splitters repeat, so the range is split in
+    equality mode and every key lands in a bucket of one value, which is only
+    copied: one K-way level, no two-way pass."""
+    n = 2_000_003
+    a = make(dtype, n, "distinct16", seed=21)
+    check_sort(vq, oracle_mod, dtype, a, True)
+    st = vq.stats()
+    assert st["kway_ranges"] == 1
+    assert st["equal_keys"] == n
+    assert st["keys_partitioned"] == n
+
+
+@pytest.mark.parametrize("dtype", ("u64", "u32", "f64"))
+@pytest.mark.parametrize("ascending", (True, False))
+def test_kway_equality_buckets_mixed(vq, oracle_mod, dtype, ascending):
+    """Half the keys one repeated value, half uniform: the repeated value gets
+    an equality bucket, the uniform keys around it are split further."""
+    n = 3_000_017
+    a = make(dtype, n, "uniform", seed=22)
+    a[::2] = a[7]
+    check_sort(vq, oracle_mod, dtype, a, ascending)
+    st = vq.stats()
+    assert st["equal_keys"] >= n // 2
+    assert st["leaf_keys"] + st["equal_keys"] + st["fallback_keys"] == n
