@@ -116,9 +116,11 @@ vq_status vqsort_sort_segmented_ws(vq_dtype dt, void *d_keys, size_t n_total,
                                    const uint64_t *d_offsets, size_t num_segments,
                                    int ascending, void *d_ws, size_t ws_bytes, void *stream);
 
-/* End-to-end sort of a HOST array: copies h_keys to the device, sorts,
-   copies back and waits. Uses a library-owned stream and device buffer on
-   the current device. h_keys may be pageable; pinned memory is faster. */
+/* End-to-end sort of a HOST array: copies h_keys to the device, sorts, and
+   waits. Uses a library-owned stream and device buffer on the current
+   device. If h_keys is pinned (page-locked and mapped), the leaf kernels
+   write the sorted keys straight into it, so the download overlaps the
+   leaves' work; pageable memory is copied back after the sort. */
 vq_status vqsort_sort_host(vq_dtype dt, void *h_keys, size_t n, int ascending);
 
 /* ---------------------------------------------------------------------- */

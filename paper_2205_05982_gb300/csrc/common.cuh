@@ -373,6 +373,8 @@ enum : unsigned int {
 struct SortArgs {
   void *keys;                 // user buffer (parity 0)
   void *alt;                  // alternate buffer (parity 1)
+  void *out;                  // where leaves and the fallback write the sorted keys: the user
+                              // buffer, or a device-accessible host buffer of the same keys
   Header *hdr;
   SegDesc *segs;
   unsigned long long *items;

@@ -132,7 +132,7 @@ template <int KB> __global__ void __launch_bounds__(FB_NT) k_fallback(SortArgs a
     // decode into the user's buffer
     const uint64_t gt = (uint64_t)blockIdx.x * FB_NT + tid, stride = (uint64_t)gridDim.x * FB_NT;
     for (uint64_t j = gt; j < len; j += stride)
-      store_key<KB>(a.keys, b + j, decode<KB>(load_cg<KB>(cur, b + j), a.codec));
+      store_key<KB>(a.out, b + j, decode<KB>(load_cg<KB>(cur, b + j), a.codec));
     if (!grid_sync(a)) return;
   }
 }

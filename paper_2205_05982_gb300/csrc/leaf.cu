@@ -55,7 +55,7 @@ __device__ __forceinline__ void warp_leaf(const SortArgs &a, const void *src, ui
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const unsigned i = lane * R + r;
-    if (i < len) store_key<KB>(a.keys, b + i, decode<KB>(k[r], a.codec));
+    if (i < len) store_key<KB>(a.out, b + i, decode<KB>(k[r], a.codec));
   }
   if (lane == 0) atomicAdd(&a.hdr->leaf_ce, network_ce<32, R>());
 }
@@ -109,7 +109,7 @@ __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, u
     sx[i + (i >> 5)] = k[r];
   }
   __syncthreads();
-  for (unsigned j = t; j < len; j += NT) store_key<KB>(a.keys, b + j, decode<KB>(sx[j + (j >> 5)], a.codec));
+  for (unsigned j = t; j < len; j += NT) store_key<KB>(a.out, b + j, decode<KB>(sx[j + (j >> 5)], a.codec));
   if (t == 0) atomicAdd(&a.hdr->leaf_ce, network_ce<NT, R>());
   __syncthreads();
 }
@@ -147,7 +147,7 @@ template <int KB, int NT> __global__ void __launch_bounds__(NT, NT <= 512 ? 2 : 
     if (le.flags & LEAF_COPY) {
       for (unsigned j = threadIdx.x; j < len; j += NT) {
         const C c = load_key<KB>(src, le.begin + j);
-        store_key<KB>(a.keys, le.begin + j, decode<KB>(raw ? encode<KB>(c, a.codec) : c, a.codec));
+        store_key<KB>(a.out, le.begin + j, decode<KB>(raw ? encode<KB>(c, a.codec) : c, a.codec));
       }
       continue;
     }

@@ -1040,7 +1040,10 @@ template <int KB> __global__ void __launch_bounds__(NT) k_seed(SortArgs a) {
       make_segment<KB>(a, b, e, 0, SEG_RAW, code_of<KB>(a.pivot.lo, a.pivot.hi), 1, rs);
       continue;
     }
-    if (m <= 1) continue;   // one key in input form is already its own output
+    if (m <= 1) {   // one key in input form is already sorted
+      if (m == 1 && a.out != a.keys && threadIdx.x == 0) store_key<KB>(a.out, b, load_cg<KB>(a.keys, b));
+      continue;
+    }
     const unsigned limit =
         a.depth_override >= 0 ? (unsigned)a.depth_override : 2 * floor_log2_u64(m) + 4;
     if (m <= a.leaf_cutoff) {

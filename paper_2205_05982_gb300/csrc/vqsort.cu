@@ -248,6 +248,7 @@ struct Job {
   unsigned mode;
   const void *pivot_host;
   uint64_t *out_left;
+  void *out = nullptr;             // sorted keys go here (default: keys)
 };
 
 vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
@@ -271,6 +272,7 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   unsigned char *w = (unsigned char *)ws;
   SortArgs a{};
   a.keys = j.keys;
+  a.out = j.out ? j.out : j.keys;
   a.alt = with_alt ? (void *)(w + L.alt) : j.alt_given;
   a.hdr = (Header *)(w + L.hdr);
   a.segs = (SegDesc *)(w + L.segs);
@@ -449,10 +451,33 @@ vq_status vqsort_sort_host(vq_dtype dt, void *h_keys, size_t n, int ascending) {
     }
     hc->dbytes = bytes;
   }
+  // A pinned (page-locked, mapped) host buffer is written by the leaf kernels
+  // themselves: the download then runs during the leaves' network work
+  // instead of after it. Other host memory is copied back.
+  void *h_dev = nullptr;
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, h_keys) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+      attr.devicePointer)
+    h_dev = attr.devicePointer;
+  cudaGetLastError();
   if (cudaMemcpyAsync(hc->dbuf, h_keys, bytes, cudaMemcpyHostToDevice, hc->stream) != cudaSuccess)
     return VQ_ERR_CUDA;
-  if ((st = sort_common(dt, hc->dbuf, n, nullptr, 1, ascending, nullptr, 0, hc->stream)) != VQ_OK) return st;
-  if (cudaMemcpyAsync(h_keys, hc->dbuf, bytes, cudaMemcpyDeviceToHost, hc->stream) != cudaSuccess)
+  {
+    const int kb = key_bytes(dt);
+    int64_t dl;
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      dl = g_depth_limit;
+    }
+    const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb), dl, true, tile_cpt(kb));
+    void *ws;
+    size_t wsb;
+    if ((st = owned_ws(hc->stream, L.total, &ws, &wsb)) != VQ_OK) return st;
+    Job j{dt, hc->dbuf, nullptr, n, nullptr, 1, ascending, MODE_SORT, nullptr, nullptr};
+    j.out = h_dev;
+    if ((st = run(j, ws, wsb, hc->stream)) != VQ_OK) return st;
+  }
+  if (!h_dev && cudaMemcpyAsync(h_keys, hc->dbuf, bytes, cudaMemcpyDeviceToHost, hc->stream) != cudaSuccess)
     return VQ_ERR_CUDA;
   return vqsort_last_device_status(nullptr, hc->stream);
 }

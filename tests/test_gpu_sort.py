@@ -234,6 +234,43 @@ def test_host_entry(vq, oracle_mod):
     assert same_bits(b, want)
 
 
+def pinned_like(a):
+    """A page-locked host copy of `a` (numpy view of a pinned torch buffer)."""
+    import torch
+    buf = torch.empty(a.nbytes, dtype=torch.uint8, pin_memory=True)
+    v = buf.numpy().view(a.dtype).reshape(a.shape)
+    v[...] = a
+    return buf, v
+
+
+@pytest.mark.parametrize("dtype,n,dist", [
+    ("u64", 3_000_017, "uniform"), ("f32", 2_000_003, "uniform"), ("i16", 1_000_001, "distinct16"),
+    ("u128", 500_009, "uniform"), ("kv64", 300_007, "uniform"), ("u32", 100_000, "equal"),
+    ("u64", 1, "uniform"), ("f64", 5000, "uniform")])
+@pytest.mark.parametrize("ascending", (True, False))
+def test_host_entry_pinned(vq, oracle_mod, dtype, n, dist, ascending):
+    """Pinned host buffers are written by the leaf kernels directly."""
+    a = make(dtype, n, dist, seed=n % 101)
+    want = oracle_mod.sort(a, dtype, ascending)
+    keep, b = pinned_like(a)
+    vq.sort_host(b, dtype, descending=not ascending)
+    assert same_bits(b, want)
+
+
+@pytest.mark.parametrize("limit", (0, 2))
+def test_host_entry_pinned_fallback(vq, oracle_mod, limit):
+    """The depth-bound merge fallback writes the pinned buffer too."""
+    a = make("u64", 200_003, "uniform", seed=3)
+    want = oracle_mod.sort(a, "u64", True)
+    vq.set_option("depth_limit", limit)
+    try:
+        keep, b = pinned_like(a)
+        vq.sort_host(b, "u64")
+    finally:
+        vq.set_option("depth_limit", -1)
+    assert same_bits(b, want)
+
+
 def test_stats_are_consistent(vq):
     import torch
     n = 10_000_000
