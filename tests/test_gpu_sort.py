@@ -396,3 +396,19 @@ def test_kway_equality_buckets_mixed(vq, oracle_mod, dtype, ascending):
     st = vq.stats()
     assert st["equal_keys"] >= n // 2
     assert st["leaf_keys"] + st["equal_keys"] + st["fallback_keys"] == n
+
+
+@pytest.mark.parametrize("threads", (256, 512, 1024))
+@pytest.mark.parametrize("cutoff", (0, 4096, 16384))
+def test_leaf_threads_with_any_cutoff(vq, oracle_mod, threads, cutoff):
+    """A leaf thread count too small for the cutoff (16 keys per thread) is
+    raised to cutoff/16; every combination sorts correctly."""
+    vq.set_option("leaf_threads", threads)
+    vq.set_option("leaf_cutoff", cutoff)
+    try:
+        for dtype in ("u64", "u32"):
+            a = make(dtype, 400_003, "uniform", seed=threads + cutoff)
+            check_sort(vq, oracle_mod, dtype, a, True)
+    finally:
+        vq.set_option("leaf_threads", 0)
+        vq.set_option("leaf_cutoff", 0)
