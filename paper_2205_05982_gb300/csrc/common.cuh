@@ -42,9 +42,28 @@ template <> struct KT<16> {   // u128 and kv64: {lo, hi} words
 
 __host__ __device__ __forceinline__ bool lt(uint32_t a, uint32_t b) { return a < b; }
 __host__ __device__ __forceinline__ bool lt(uint64_t a, uint64_t b) { return a < b; }
-// Algorithm 2: the upper word decides unless equal, then the lower word.
+// Algorithm 2: the upper word decides unless equal, then the lower word. On
+// the device the same order is read from the borrow of the 128-bit
+// subtraction a - b (four chained 32-bit subtractions): a < b exactly when it
+// borrows.
 __host__ __device__ __forceinline__ bool lt(const U128 &a, const U128 &b) {
+#ifdef __CUDA_ARCH__
+  unsigned borrow;
+  asm("{\n\t"
+      ".reg .u32 t;\n\t"
+      "sub.cc.u32 t, %1, %5;\n\t"
+      "subc.cc.u32 t, %2, %6;\n\t"
+      "subc.cc.u32 t, %3, %7;\n\t"
+      "subc.cc.u32 t, %4, %8;\n\t"
+      "subc.u32 %0, 0, 0;\n\t"
+      "}"
+      : "=r"(borrow)
+      : "r"((unsigned)a.lo), "r"((unsigned)(a.lo >> 32)), "r"((unsigned)a.hi), "r"((unsigned)(a.hi >> 32)),
+        "r"((unsigned)b.lo), "r"((unsigned)(b.lo >> 32)), "r"((unsigned)b.hi), "r"((unsigned)(b.hi >> 32)));
+  return borrow != 0;
+#else
   return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+#endif
 }
 __host__ __device__ __forceinline__ bool eq(uint32_t a, uint32_t b) { return a == b; }
 __host__ __device__ __forceinline__ bool eq(uint64_t a, uint64_t b) { return a == b; }
