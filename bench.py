@@ -74,6 +74,9 @@ def dist_env():
     return rank, world, local
 
 
+METRIC = "sort throughput (GKeys/s), 1e8 keys per array"
+
+
 def partition_bytes(kb: int, st: dict) -> int:
     """Algorithmic bytes of one partition launch: every partitioned key is
     read and written once (two-way and K-way scatter passes), and K-way
@@ -153,7 +156,7 @@ def run_reference(args):
     a = make_input(args)
     cb = cpu_baseline(args, a, max(3.0, args.cpu_seconds))
     line = {
-        "impl": "reference", "metric": "sort throughput (GKeys/s)", "value": cb["value"],
+        "impl": "reference", "metric": METRIC, "value": cb["value"],
         "unit": "GKeys/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
         "data": "synthetic", "config": workload(args), "cpu_baseline": cb,
@@ -531,7 +534,7 @@ def run_gpu(args):
         e2e_val = world * args.n * len(e2e_times) / sum(e2e_times) / 1e9
 
     line = {
-        "metric": "sort throughput (GKeys/s), 1e8 keys per array",
+        "metric": METRIC,
         "value": world * args.n / (ms_step * 1e-3) / 1e9,
         "unit": "GKeys/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
