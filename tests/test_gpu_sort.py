@@ -412,3 +412,28 @@ def test_leaf_threads_with_any_cutoff(vq, oracle_mod, threads, cutoff):
     finally:
         vq.set_option("leaf_threads", 0)
         vq.set_option("leaf_cutoff", 0)
+
+
+@pytest.mark.parametrize("ascending", (True, False))
+def test_beyond_2_pow_31_keys(vq, ascending):
+    """2^31 + 12345 u16 keys (4.3 GB), generated on the device: key indices,
+    tile numbers and range cursors pass 2^31. The output must be sorted and
+    hold the same multiset (its 65536-bin histogram); both are exact."""
+    import torch
+    n = (1 << 31) + 12345
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1234)
+    t = torch.randint(-32768, 32768, (n,), dtype=torch.int16, device="cuda", generator=g)
+    want_hist = torch.bincount(t.view(torch.int16).to(torch.int32) + 32768, minlength=65536)
+    vq.sort_(t, "u16", descending=not ascending)
+    assert vq.last_device_status() == 0
+    assert vq.stats()["guard"] == 0
+    u = t.to(torch.int32) & 0xFFFF   # the u16 values
+    step = 1 << 28
+    for s0 in range(0, n - 1, step):   # adjacent pairs, in slices to bound memory
+        a_, b_ = u[s0:min(n - 1, s0 + step)], u[s0 + 1:min(n, s0 + step + 1)]
+        ok = bool((b_ >= a_).all()) if ascending else bool((b_ <= a_).all())
+        assert ok, s0
+    assert torch.equal(torch.bincount(t.to(torch.int32) + 32768, minlength=65536), want_hist)
+    del t, u
+    torch.cuda.empty_cache()
