@@ -1,17 +1,19 @@
 // The Quicksort recursion on the device: pivot sampling (Sec. 2.2), the
 // partition level (Sec. 2.1) and the recursion driver (Algorithm 1) as one
-// persistent kernel pulling tiles from an on-device work queue.
+// persistent kernel pulling work from an on-device queue.
 //
-// A live range ("segment") [begin, end) of the recursion is cut into tiles of
-// T keys; each tile is one queue item. A thread block claims the next item,
-// loads the tile with one TMA bulk copy into shared memory, compares every
-// key with the pivot, compacts left and right keys inside the block with
-// warp ballots, learns how many left keys all earlier tiles of the range
-// produced by decoupled look-back, and writes both runs to the other
-// (ping-pong) buffer: left keys grow from `begin`, right keys from `end`
-// downwards. The block that finishes the last tile of a range performs the
-// rest of Algorithm 1 for it: the degenerate-partition rule, leaf routing of
-// small children, the depth bound, pivot sampling of large children, and
+// A live range ("segment") [begin, end) of the recursion is cut into tiles;
+// each tile is one queue item. A thread block claims the next item and loads
+// the tile with one TMA bulk copy into shared memory. A two-way range
+// compares every key with the pivot, compacts left and right keys with warp
+// ballots, reserves its slots on both sides with one atomic on the range's
+// write cursors and writes both runs to the other (ping-pong) buffer: left
+// keys grow from `begin`, right keys from `end` downwards. A K-way range (16
+// to 256 buckets, the multi-pivot split of Sec. 4.2) runs a counting pass and
+// a scatter pass over its tiles. The block that finishes the last tile of a
+// range performs the rest of Algorithm 1 for it: the degenerate-partition
+// rule, leaf routing of small children, the depth bound, pivot sampling of
+// children (large ones through setup items that any block can claim), and
 // publication of their tiles as new queue items. No step needs the host.
 #include "launch.h"
 #include "sortnet.cuh"
@@ -781,7 +783,7 @@ __device__ void finish_range(const SortArgs &a, const SegDesc &sd, unsigned sid,
 }
 
 // ---------------------------------------------------------------------------
-// Work claiming and look-back.
+// Work claiming.
 // ---------------------------------------------------------------------------
 
 // Thread 0: waits (bounded) for the item of an already claimed ticket.
