@@ -65,7 +65,8 @@ typedef enum vq_status {
    workspace the library allocates and keeps for this (device, stream).
    The recursion runs on the device: a persistent kernel pulls partition
    tiles from an on-device work queue (Sec. 2.1 partition, Sec. 2.2 pivot
-   sampling, Algorithm 1 degenerate rule), small ranges are finished by
+   sampling, Algorithm 1 degenerate rule; large ranges are split into up to
+   256 buckets per level, Sec. 4.2), small ranges are finished by
    sorting networks (Sec. 2.3, Sec. 3), and ranges deeper than
    2*floor(log2 n)+4 partition levels go to a device merge sort (the
    paper's Heapsort fallback of Sec. 2.2, replaced). */
@@ -225,12 +226,15 @@ typedef enum vq_option {
   VQ_OPT_TILE_BYTES = 5,    /* partition tile window: 16384, 32768 or 65536 bytes; 0 (default):
                                64 KiB for 8- and 16-byte keys, 32 KiB for narrower keys */
   VQ_OPT_LEAF_THREADS = 6,  /* 0: block leaves use cutoff/16 threads (16 keys per thread);
-                               256, 512 or 1024: that many threads, so cutoff/threads keys
-                               per thread (at most 16); ignored for 16-byte keys */
-  VQ_OPT_KWAY = 7           /* 1 (default): ranges of >= 2^18 keys are split 16 ways per
-                               level (15 sampled splitters, a counting pass and a scatter
-                               pass; the K > 2 partition of Sec. 4.2); 0: every level is the
-                               paper's two-way Partition. The output is the same. */
+                               256, 512 or 1024: that many threads when they hold a
+                               cutoff-size leaf at 16 keys each (else cutoff/16); 16-byte
+                               keys: 256 or (otherwise) 512 threads */
+  VQ_OPT_KWAY = 7           /* 1 (default): ranges of at least 4x the leaf cutoff are split
+                               into 16..256 buckets per level (sampled splitters, a counting
+                               pass and a scatter pass; the K > 2 partition of Sec. 4.2),
+                               with equality buckets when the splitters repeat; 0: every
+                               level is the paper's two-way Partition. The output is the
+                               same. */
 } vq_option;
 vq_status vqsort_set_option(vq_option opt, int64_t value);
 int64_t vqsort_get_option(vq_option opt);
