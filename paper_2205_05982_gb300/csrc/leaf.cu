@@ -122,7 +122,8 @@ template <int KB, int NT> __host__ __device__ constexpr int leaf_rmax() {
 
 // NT threads sort one range of up to RMAX*NT keys, R = P/NT keys per thread
 // where P is the range length rounded up to a power of two (>= NT).
-template <int KB, int NT> __global__ void __launch_bounds__(NT, NT <= 512 ? 2 : 1) k_leaf_block(SortArgs a) {
+template <int KB, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 && KB <= 8 ? 4 : NT <= 512 ? 2 : 1) k_leaf_block(SortArgs a) {
   constexpr int RMAX = leaf_rmax<KB, NT>();
   using C = typename KT<KB>::Code;
   extern __shared__ __align__(16) unsigned char smem[];
