@@ -196,9 +196,6 @@ __device__ unsigned long long reserve(const SortArgs &a, unsigned long long *cou
   return i;
 }
 
-// A finished range of keys that only needs sorting by a leaf network, or
-// only decoding (all equal), or the merge fallback. Returns the keys handed
-// over (counted off `remaining` by the caller).
 // The leaf list for a range of m keys (at most the cutoff): warp leaves up to
 // WARP_LEAF_MAX keys, mid-size leaves up to a.mid_max, block leaves above.
 struct LeafList {
@@ -212,6 +209,10 @@ __device__ __forceinline__ LeafList leaf_list(const SortArgs &a, uint64_t m) {
   return LeafList{&a.hdr->n_leaf_block, &a.hdr->leaves_block, a.leaf_block, a.cap_leaf_block};
 }
 
+// A finished range of keys that only needs sorting by a leaf network
+// (emit_leaf), or only decoding because all keys are equal (emit_equal), or
+// the merge fallback (emit_fallback). The caller counts the keys handed over
+// off `remaining`.
 __device__ void emit_leaf(const SortArgs &a, uint64_t b, uint64_t m, unsigned flags, RangeScratch &rs) {
   const LeafList L = leaf_list(a, m);
   const unsigned long long i = reserve(a, L.n, L.cap, 1, rs);
@@ -253,7 +254,10 @@ __device__ void emit_fallback(const SortArgs &a, uint64_t b, uint64_t m, unsigne
 // counting pass and one scatter pass, where two-way levels would need kbits
 // passes. Splitters come from a sorted random sample; bucket j holds the keys
 // above splitter j and at most splitter j+1 (keys equal to a splitter take
-// the lower bucket, the "<=" rule of the two-way partition). A key's bucket
+// the lower bucket, the "<=" rule of the two-way partition). When the
+// splitters repeat values, the range switches to equality mode: 2d + 1
+// buckets around its d distinct splitters, every second one holding the keys
+// equal to one splitter (build_splitters). A key's bucket
 // is found through a table indexed by the KW_TABLE_BITS code bits that follow
 // the prefix shared by the first and the last splitter: the table gives the
 // splitters certainly below the key and the few (usually none or one) that
@@ -805,11 +809,6 @@ __device__ int wait_ticket(const SortArgs &a, unsigned long long t, unsigned lon
     }
     __nanosleep(it < 32 ? 32 : 256);
   }
-}
-
-// Thread 0: claims the next ticket and waits for its item.
-__device__ int claim(const SortArgs &a, unsigned long long &item) {
-  return wait_ticket(a, atomicAdd(&a.hdr->head, 1ull), item);
 }
 
 // Thread 0: is the item of ticket t already published?
