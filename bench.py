@@ -291,6 +291,26 @@ def extra_dtypes(vq, torch, peak, n):
     return out
 
 
+def extra_wide(vq, torch, peak, n=25_000_000):
+    """Wide keys: 2.5e7 u128 keys (two uniform halves) and 2.5e7 kv64 pairs
+    (uniform key, value = index, 10 % of keys duplicated)."""
+    out = {}
+    for dt in ("u128", "kv64"):
+        a = inputs.kv_pairs(n) if dt == "kv64" else inputs.make(dt, n, "uniform")
+        src = to_device_bits(a, dt, torch)
+        copies = [src.clone() for _ in range(4)]
+        ws = vq.alloc_workspace(dt, n)
+        ms, st, prof = time_sorts(vq, torch, copies, ws, dt, 1)
+        part = prof.get("partition", {"ms": float("nan"), "launches": 1})
+        part_ms = part["ms"] / max(1, part["launches"])
+        out[dt] = {"gkeys_per_s": n / (ms * 1e-3) / 1e9, "ms": ms,
+                   "partition_frac": partition_bytes(16, st) / (part_ms * 1e-3) / 1e9 / peak,
+                   "leaf_ms": sum(v["ms"] for k, v in prof.items() if k.startswith("leaf")) / max(1, part["launches"])}
+        del copies, src, ws
+        torch.cuda.empty_cache()
+    return out
+
+
 def extra_stable(vq, torch, n, reps=5):
     """Stable sorts (Sec. 5 row-id recipe) of n uniform keys: keys of up to 4
     bytes travel as 64-bit (code, row) codes, 8-byte keys as 128-bit ones."""
@@ -577,6 +597,7 @@ def run_gpu(args):
             del src
             torch.cuda.empty_cache()
             line["per_dtype"] = extra_dtypes(vq, torch, peak, args.n)
+            line["wide"] = extra_wide(vq, torch, peak)
             line["partition_sweep"] = extra_partition_sweep(vq, torch, peak)
             line["stable"] = extra_stable(vq, torch, args.n)
             line["batched"] = extra_batched(vq, torch)
