@@ -33,19 +33,35 @@ from paper_2205_05982_gb300 import inputs  # noqa: E402
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-# sources of the partition kernel: a recorded DRAM traffic figure is used
-# only while these files are unchanged since the capture
+# sources of the partition and leaf kernels: a recorded DRAM traffic figure
+# is used only while these files are unchanged since the capture
 KERNEL_SOURCES = ("paper_2205_05982_gb300/csrc/partition.cu", "paper_2205_05982_gb300/csrc/common.cuh",
                   "paper_2205_05982_gb300/csrc/launch.h")
+LEAF_SOURCES = ("paper_2205_05982_gb300/csrc/leaf.cu", "paper_2205_05982_gb300/csrc/sortnet.cuh",
+                "paper_2205_05982_gb300/csrc/networks.h", "paper_2205_05982_gb300/csrc/common.cuh",
+                "paper_2205_05982_gb300/csrc/launch.h")
 
 
-def kernel_hash() -> str:
+def kernel_hash(sources=KERNEL_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def recorded_traffic(key: str, sources) -> int | None:
+    """DRAM bytes per launch recorded in profiles/traffic.json for `key`, if
+    the kernel's sources still hash to the captured build."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        if key in tr and tr[key].get("kernel_hash") == kernel_hash(sources):
+            return tr[key]["bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
 
 
 def parse():
@@ -524,15 +540,7 @@ def run_gpu(args):
     part_bytes = partition_bytes(kb, st)
     peak, peak_kind = hbm_peak()
     achieved = part_bytes / (part_ms * 1e-3) / 1e9
-    traffic = None
-    try:
-        with open(TRAFFIC_FILE) as f:
-            tr = json.load(f)
-        key = f"{args.dtype}:{args.n}:{args.dist}"
-        if key in tr and tr[key].get("kernel_hash") == kernel_hash():
-            traffic = tr[key]["bytes_per_launch"]
-    except Exception:  # noqa: BLE001
-        pass
+    traffic = recorded_traffic(f"{args.dtype}:{args.n}:{args.dist}", KERNEL_SOURCES)
     leaf_ms = sum(v["ms"] for k, v in prof.items() if k.startswith("leaf")) / args.steps
     sort_bytes = part_bytes + 2 * kb * args.n
     kernels = {k: {"ms_per_launch": v["ms"] / max(1, v["launches"]), "launches": v["launches"]}
@@ -588,7 +596,8 @@ def run_gpu(args):
     leaf_achieved = leaf_ops / (leaf_ms * 1e-3) if leaf_ms > 0 else 0.0
     line["roofline_leaf"] = {"bound": "alu", "kernel": "k_leaf_warp + k_leaf_mid + k_leaf_block (sorting networks)",
                              "achieved": leaf_achieved / 1e12, "peak": apeak / 1e12, "unit": "Tlane-op/s",
-                             "frac": leaf_achieved / apeak, "peak_source": apeak_kind, "traffic": None,
+                             "frac": leaf_achieved / apeak, "peak_source": apeak_kind,
+                             "traffic": recorded_traffic(f"leaf:{args.dtype}:{args.n}:{args.dist}", LEAF_SOURCES),
                              "compare_exchanges_per_step": ce, "ops_per_compare_exchange": ALU_OPS_PER_CE[kb]}
     # the dominant kernel by measured time decides which one is "roofline"
     line["roofline"] = dict(line["roofline_leaf"] if leaf_ms > part_ms else line["roofline_partition"])
