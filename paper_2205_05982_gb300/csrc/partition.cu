@@ -328,7 +328,22 @@ __device__ __forceinline__ unsigned classify(const C &k, const C *split, const u
   // table bits is below k and every one with larger bits above it
   const unsigned e = table[table_bits(k, sh)];
   unsigned b = e & 255u, n = e >> 8;
-  while (n) {   // count the ones with equal bits that are below k
+  // Count the splitters with equal table bits that are below k. Most keys
+  // have none or one: the first candidate is compared without a branch
+  // (loaded even when there is none, from a valid slot), and only a key above
+  // it with more candidates left enters the search loop.
+  {
+    const bool below = lt(split[b < KW_MAX - 1 ? b + 1 : KW_MAX - 1], k);
+    if (n) {
+      if (below) {
+        ++b;
+        --n;
+      } else {
+        n = 0;
+      }
+    }
+  }
+  while (n) {
     const unsigned h = n >> 1;
     if (lt(split[b + h + 1], k)) {
       b += h + 1;
