@@ -907,9 +907,9 @@ __device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *sw,
 // Counting pass over a K-way tile window: every key adds one to its bucket's
 // shared histogram.
 template <int KB, int KCPT, bool RAW>
-__device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
-                                              unsigned hi, const KwLookup<typename KT<KB>::Code> &cl,
-                                              unsigned *s_hist, unsigned char *ids) {
+__device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *__restrict__ sw, unsigned nwc,
+                                              unsigned lo, unsigned hi, const KwLookup<typename KT<KB>::Code> &cl,
+                                              unsigned *__restrict__ s_hist, unsigned char *__restrict__ ids) {
   using C = typename KT<KB>::Code;
   constexpr unsigned V = 16 / KB;
 #pragma unroll
@@ -942,13 +942,14 @@ __device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *sw
 // with consecutive threads on consecutive keys, so each bucket's keys leave
 // as one contiguous run.
 template <int KB, int KCPT, bool RAW>
-__device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
-                                                unsigned hi, const unsigned char *s_ids, unsigned K,
-                                                KwayDesc &kw, unsigned stripe, uint64_t rbegin,
-                                                typename KT<KB>::Mem *dst,
-                                                typename KT<KB>::Mem *stage, unsigned char *sb,
-                                                unsigned *s_hist, unsigned short *s_tstart, unsigned *s_off,
-                                                unsigned long long *s_w) {
+__device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *__restrict__ sw, unsigned nwc,
+                                                unsigned lo, unsigned hi, const unsigned char *__restrict__ s_ids,
+                                                unsigned K, KwayDesc &kw, unsigned stripe, uint64_t rbegin,
+                                                typename KT<KB>::Mem *__restrict__ dst,
+                                                typename KT<KB>::Mem *__restrict__ stage,
+                                                unsigned char *__restrict__ sb, unsigned *__restrict__ s_hist,
+                                                unsigned short *__restrict__ s_tstart,
+                                                unsigned *__restrict__ s_off, unsigned long long *s_w) {
   using C = typename KT<KB>::Code;
   constexpr unsigned V = 16 / KB, Q = KCPT * V;
   const unsigned tid = threadIdx.x;
@@ -1011,7 +1012,8 @@ __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *
     }
   }
   __syncthreads();
-  typename KT<KB>::Mem *out = dst + rbegin;
+  typename KT<KB>::Mem *__restrict__ out = dst + rbegin;
+#pragma unroll 4
   for (unsigned p = tid; p < (unsigned)nkeys; p += NT) {
     const unsigned off = s_off[sb[p]];
     if (off != ~0u) out[off + p] = stage[p];
