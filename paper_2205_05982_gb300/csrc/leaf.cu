@@ -109,7 +109,9 @@ __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, u
     sx[i + (i >> 5)] = k[r];
   }
   __syncthreads();
-  for (unsigned j = t; j < len; j += NT) store_key<KB>(a.out, b + j, decode<KB>(sx[j + (j >> 5)], a.codec));
+  const C *__restrict__ st = sx;
+#pragma unroll 4
+  for (unsigned j = t; j < len; j += NT) store_key<KB>(a.out, b + j, decode<KB>(st[j + (j >> 5)], a.codec));
   if (t == 0) atomicAdd(&a.hdr->leaf_ce, network_ce<NT, R>());
   __syncthreads();
 }

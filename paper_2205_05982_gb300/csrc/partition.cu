@@ -846,7 +846,7 @@ template <int KB> __device__ __forceinline__ typename KT<KB>::Mem to_mem(typenam
 // whether some key is < pivot. Chunks fully inside the tile skip the
 // per-key bounds test.
 template <int KB, int CPT, bool RAW>
-__device__ __forceinline__ void count_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
+__device__ __forceinline__ void count_tile(const SortArgs &a, const uint4 *__restrict__ sw, unsigned nwc, unsigned lo,
                                            unsigned hi, typename KT<KB>::Code piv, unsigned &nL,
                                            unsigned &nV, int &anyLt) {
   using C = typename KT<KB>::Code;
@@ -872,9 +872,10 @@ __device__ __forceinline__ void count_tile(const SortArgs &a, const uint4 *sw, u
 // Pass 2 over the tile window: every valid key goes to its ballot rank in
 // the left run (outL) or the right run (outR).
 template <int KB, int CPT, bool RAW, bool DEC>
-__device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *sw, unsigned nwc, unsigned lo,
-                                             unsigned hi, typename KT<KB>::Code piv,
-                                             typename KT<KB>::Mem *outL, typename KT<KB>::Mem *outR,
+__device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *__restrict__ sw, unsigned nwc,
+                                             unsigned lo, unsigned hi, typename KT<KB>::Code piv,
+                                             typename KT<KB>::Mem *__restrict__ outL,
+                                             typename KT<KB>::Mem *__restrict__ outR,
                                              unsigned runL, unsigned runR) {
   using C = typename KT<KB>::Code;
   constexpr unsigned V = 16 / KB;
