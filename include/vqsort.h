@@ -124,6 +124,16 @@ vq_status vqsort_sort_segmented_ws(vq_dtype dt, void *d_keys, size_t n_total,
    leaves' work; pageable memory is copied back after the sort. */
 vq_status vqsort_sort_host(vq_dtype dt, void *h_keys, size_t n, int ascending);
 
+/* The same end-to-end sort of a HOST array, enqueued on `stream` without
+   waiting: the upload, the sort and the download (or the leaves' direct
+   writes into a pinned array) follow one another on that stream, and h_keys
+   must stay untouched until the stream has passed them. The device copy and
+   the workspace belong to the library, one per (device, stream), so arrays
+   on different streams overlap: one uploads while another sorts and writes
+   back. Completion: synchronize the stream; the status is then read with
+   vqsort_last_device_status(NULL, stream). */
+vq_status vqsort_sort_host_async(vq_dtype dt, void *h_keys, size_t n, int ascending, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* The two per-level kernels on their own.                                 */
 /* ---------------------------------------------------------------------- */

@@ -75,6 +75,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "vqsort_sort": ([i32, vp, sz, i32, vp], i32),
         "vqsort_sort_kv": ([vp, sz, i32, vp], i32),
         "vqsort_sort_stable": ([i32, vp, sz, i32, vp, vp], i32),
+        "vqsort_sort_host_async": ([i32, vp, sz, i32, vp], i32),
         "vqsort_sort_segmented": ([i32, vp, sz, vp, sz, i32, vp], i32),
         "vqsort_workspace_bytes": ([i32, sz, sz], sz),
         "vqsort_sort_ws": ([i32, vp, sz, i32, vp, sz, vp], i32),
@@ -249,6 +250,19 @@ def sort_host(array, dtype: str, descending: bool = False):
            "vqsort_sort_host")
     if a is not array:
         array[...] = a
+    return array
+
+
+def sort_host_async(array, dtype: str, descending: bool = False, stream=None):
+    """Enqueues the end-to-end sort of a C-contiguous host numpy array on
+    `stream` (a torch.cuda.Stream or None) and returns at once; the array
+    holds the sorted keys once the stream has passed the call. Keep the
+    array alive and untouched until then."""
+    if not array.flags["C_CONTIGUOUS"]:
+        raise ValueError("sort_host_async needs a C-contiguous array")
+    n = array.shape[0] if KEY_BYTES[dtype] == 16 else array.size
+    _check(load().vqsort_sort_host_async(CODE[dtype], ctypes.c_void_p(array.ctypes.data), n, int(not descending),
+                                         _stream(stream)), "vqsort_sort_host_async")
     return array
 
 

@@ -365,10 +365,14 @@ vq_status sort_common(vq_dtype dt, void *keys, uint64_t n, const uint64_t *offse
 // Library-owned resources of the host entry point.
 struct HostCtx {
   cudaStream_t stream = nullptr;
-  void *dbuf = nullptr;
-  size_t dbytes = 0;
 };
 std::map<int, HostCtx> g_host;
+// Device copies of host arrays, one per (device, stream).
+struct DevBuf {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+std::map<std::pair<int, cudaStream_t>, DevBuf> g_hostbuf;
 
 vq_status read_header(const void *ws, void *stream, Header *h) {
   cudaStream_t s = (cudaStream_t)stream;
@@ -381,6 +385,57 @@ vq_status read_header(const void *ws, void *stream, Header *h) {
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) return VQ_ERR_CUDA;
   if (cudaMemcpy(h, ws, sizeof(Header), cudaMemcpyDeviceToHost) != cudaSuccess) return VQ_ERR_CUDA;
+  return VQ_OK;
+}
+
+// Uploads a host array to a device buffer owned for (device, stream), sorts
+// it and brings the keys back, all enqueued on `s`; nothing waits. A pinned
+// (page-locked, mapped) host array is written by the leaf kernels
+// themselves, so the download runs during the leaves' network work instead
+// of after it; other host memory is copied back after the sort.
+vq_status host_enqueue(vq_dtype dt, void *h_keys, size_t n, int ascending, cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VQ_ERR_CUDA;
+  const int kb = key_bytes(dt);
+  const size_t bytes = n * (size_t)kb;
+  void *dbuf = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevBuf &b = g_hostbuf[{dev, s}];
+    if (b.bytes < bytes) {
+      if (b.ptr) cudaFree(b.ptr);
+      b.ptr = nullptr;
+      b.bytes = 0;
+      if (cudaMalloc(&b.ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return VQ_ERR_NOMEM;
+      }
+      b.bytes = bytes;
+    }
+    dbuf = b.ptr;
+  }
+  void *h_dev = nullptr;
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, h_keys) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+      attr.devicePointer)
+    h_dev = attr.devicePointer;
+  cudaGetLastError();
+  if (cudaMemcpyAsync(dbuf, h_keys, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return VQ_ERR_CUDA;
+  int64_t dl;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    dl = g_depth_limit;
+  }
+  const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb), dl, true, tile_cpt(kb));
+  void *ws;
+  size_t wsb;
+  vq_status st;
+  if ((st = owned_ws(s, L.total, &ws, &wsb)) != VQ_OK) return st;
+  Job j{dt, dbuf, nullptr, n, nullptr, 1, ascending, MODE_SORT, nullptr, nullptr};
+  j.out = h_dev;
+  if ((st = run(j, ws, wsb, s)) != VQ_OK) return st;
+  if (!h_dev && cudaMemcpyAsync(h_keys, dbuf, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return VQ_ERR_CUDA;
   return VQ_OK;
 }
 
@@ -433,53 +488,24 @@ vq_status vqsort_sort_host(vq_dtype dt, void *h_keys, size_t n, int ascending) {
   if ((st = check_device()) != VQ_OK) return st;
   int dev = 0;
   cudaGetDevice(&dev);
-  HostCtx *hc;
+  cudaStream_t s;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    hc = &g_host[dev];
-    if (!hc->stream && cudaStreamCreateWithFlags(&hc->stream, cudaStreamNonBlocking) != cudaSuccess)
+    HostCtx &hc = g_host[dev];
+    if (!hc.stream && cudaStreamCreateWithFlags(&hc.stream, cudaStreamNonBlocking) != cudaSuccess)
       return VQ_ERR_CUDA;
+    s = hc.stream;
   }
-  const size_t bytes = n * (size_t)key_bytes(dt);
-  if (hc->dbytes < bytes) {
-    if (hc->dbuf) cudaFree(hc->dbuf);
-    hc->dbuf = nullptr;
-    hc->dbytes = 0;
-    if (cudaMalloc(&hc->dbuf, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      return VQ_ERR_NOMEM;
-    }
-    hc->dbytes = bytes;
-  }
-  // A pinned (page-locked, mapped) host buffer is written by the leaf kernels
-  // themselves: the download then runs during the leaves' network work
-  // instead of after it. Other host memory is copied back.
-  void *h_dev = nullptr;
-  cudaPointerAttributes attr{};
-  if (cudaPointerGetAttributes(&attr, h_keys) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
-      attr.devicePointer)
-    h_dev = attr.devicePointer;
-  cudaGetLastError();
-  if (cudaMemcpyAsync(hc->dbuf, h_keys, bytes, cudaMemcpyHostToDevice, hc->stream) != cudaSuccess)
-    return VQ_ERR_CUDA;
-  {
-    const int kb = key_bytes(dt);
-    int64_t dl;
-    {
-      std::lock_guard<std::mutex> lk(g_mu);
-      dl = g_depth_limit;
-    }
-    const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb), dl, true, tile_cpt(kb));
-    void *ws;
-    size_t wsb;
-    if ((st = owned_ws(hc->stream, L.total, &ws, &wsb)) != VQ_OK) return st;
-    Job j{dt, hc->dbuf, nullptr, n, nullptr, 1, ascending, MODE_SORT, nullptr, nullptr};
-    j.out = h_dev;
-    if ((st = run(j, ws, wsb, hc->stream)) != VQ_OK) return st;
-  }
-  if (!h_dev && cudaMemcpyAsync(h_keys, hc->dbuf, bytes, cudaMemcpyDeviceToHost, hc->stream) != cudaSuccess)
-    return VQ_ERR_CUDA;
-  return vqsort_last_device_status(nullptr, hc->stream);
+  if ((st = host_enqueue(dt, h_keys, n, ascending, s)) != VQ_OK) return st;
+  return vqsort_last_device_status(nullptr, s);
+}
+
+vq_status vqsort_sort_host_async(vq_dtype dt, void *h_keys, size_t n, int ascending, void *stream) {
+  vq_status st = check_keys(dt, h_keys, n);
+  if (st != VQ_OK) return st;
+  if (n <= 1) return VQ_OK;
+  if ((st = check_device()) != VQ_OK) return st;
+  return host_enqueue(dt, h_keys, n, ascending, (cudaStream_t)stream);
 }
 
 vq_status vqsort_partition(vq_dtype dt, const void *d_in, void *d_out, size_t n, const void *h_pivot,

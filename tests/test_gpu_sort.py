@@ -437,3 +437,28 @@ def test_beyond_2_pow_31_keys(vq, ascending):
     assert torch.equal(torch.bincount(t.to(torch.int32) + 32768, minlength=65536), want_hist)
     del t, u
     torch.cuda.empty_cache()
+
+
+def test_host_async_two_streams(vq, oracle_mod):
+    """Several host arrays, pinned and pageable, sorted on two streams at
+    once: each ends up equal to the oracle's sort."""
+    import torch
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    cases = [("u64", 3_000_017, True), ("f32", 2_000_003, False), ("i16", 1_000_001, True),
+             ("u64", 2_500_001, False), ("kv64", 300_007, True)]
+    keep, arrays, wants = [], [], []
+    for i, (dtype, n, pinned) in enumerate(cases):
+        a = make(dtype, n, "uniform", seed=40 + i)
+        wants.append(oracle_mod.sort(a, dtype, i % 2 == 0))
+        if pinned:
+            buf, v = pinned_like(a)
+            keep.append(buf)
+        else:
+            v = a.copy()
+        arrays.append(v)
+        vq.sort_host_async(v, dtype, descending=i % 2 == 1, stream=streams[i % 2])
+    for s in streams:
+        s.synchronize()
+        assert vq.last_device_status(None, s) == 0
+    for (dtype, n, _), v, w in zip(cases, arrays, wants):
+        assert same_bits(v, w), dtype
