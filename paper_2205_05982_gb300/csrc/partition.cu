@@ -477,6 +477,11 @@ __device__ unsigned build_splitters(const void *buf, uint64_t b, uint64_t m, boo
   return eqm ? 2 * (unsigned)nd + 1 : K;
 }
 
+// Counting-pass tiles of a K-way range with `nt` scatter-pass tiles: a
+// counting tile needs no staging half, so it covers two scatter tiles' keys
+// (the whole window) and keeps one histogram for each.
+__device__ __forceinline__ unsigned kw_count_items(unsigned nt) { return (nt + 1) / 2; }
+
 // Creates a K-way range on record `kid` (splitters already written) and
 // publishes its counting-pass tiles.
 __device__ void make_kway_segment(const SortArgs &a, uint64_t b, uint64_t e, unsigned depth, unsigned flags,
@@ -484,15 +489,15 @@ __device__ void make_kway_segment(const SortArgs &a, uint64_t b, uint64_t e, uns
                                   RangeScratch &rs) {
   const unsigned T = a.kw_tile_keys;
   const uint64_t m = e - b;
-  const unsigned nt = (unsigned)((m + T - 1) / T);
+  const unsigned nt = (unsigned)((m + T - 1) / T), nc = kw_count_items(nt);
   KwayDesc &kw = a.kw[kid];
   for (unsigned j = threadIdx.x; j < K; j += NT)
 #pragma unroll
     for (unsigned st = 0; st < KW_STRIPES; ++st) kw.cnt[st][j] = 0;
   if (threadIdx.x == 0) {
     const unsigned long long sid = atomicAdd(&a.hdr->nseg, 1ull);
-    const unsigned long long q0 = atomicAdd(&a.hdr->tail, (unsigned long long)nt);
-    const int ok = sid < a.cap_segs && q0 + nt <= a.cap_q && sid < (1ull << 31);
+    const unsigned long long q0 = atomicAdd(&a.hdr->tail, (unsigned long long)nc);
+    const int ok = sid < a.cap_segs && q0 + nc <= a.cap_q && sid < (1ull << 31);
     if (ok) {
       SegDesc &d = a.segs[sid];
       d.begin = b;
@@ -515,7 +520,7 @@ __device__ void make_kway_segment(const SortArgs &a, uint64_t b, uint64_t e, uns
   }
   __syncthreads();
   // the counters (zeroed above) and the descriptor are published with the items
-  if (rs.ok) publish_items(a, rs.q0, nt, ITEM_VALID | (rs.sid << 32));
+  if (rs.ok) publish_items(a, rs.q0, nc, ITEM_VALID | (rs.sid << 32));
   __syncthreads();
 }
 
@@ -648,7 +653,7 @@ __device__ void finish_kway_scatter(const SortArgs &a, const SegDesc &sd, unsign
   const uint64_t m = sd.end - sd.begin;
   if (tid == 0) {
     atomicAdd(&a.hdr->keys_partitioned, m);
-    atomicAdd(&a.hdr->tiles, 2ull * sd.ntiles);
+    atomicAdd(&a.hdr->tiles, (unsigned long long)(sd.ntiles + kw_count_items(sd.ntiles)));
     atomicAdd(&a.hdr->segments, 1ull);
     atomicAdd(&a.hdr->kway_ranges, 1ull);
     atomicMax(&a.hdr->max_depth, (unsigned long long)d1);
@@ -905,16 +910,24 @@ __device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *__r
   }
 }
 
-// Counting pass over a K-way tile window: every key adds one to its bucket's
-// shared histogram.
+// Counting pass over a K-way counting tile, the keys of two scatter tiles
+// (2 x KCPT chunks per thread): every key adds one to its bucket in the
+// histogram of the scatter tile that will move it (h0 for the first TK keys,
+// h1 for the rest), and its bucket is stored for the scatter pass. A scatter
+// tile holds TK keys, TK x KB = NT x KCPT x 16 - 16 bytes, so only the chunks
+// of j = KCPT - 1 can hold keys of both.
 template <int KB, int KCPT, bool RAW>
 __device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *__restrict__ sw, unsigned nwc,
                                               unsigned lo, unsigned hi, const KwLookup<typename KT<KB>::Code> &cl,
-                                              unsigned *__restrict__ s_hist, unsigned char *__restrict__ ids) {
+                                              unsigned *__restrict__ h0, unsigned *__restrict__ h1,
+                                              unsigned char *__restrict__ ids) {
   using C = typename KT<KB>::Code;
   constexpr unsigned V = 16 / KB;
+  constexpr unsigned TK = kw_tile_keys(KB, 2 * KCPT);
+  static_assert(TK * KB == NT * KCPT * 16 - 16, "scatter tile size");
+  const unsigned split = lo + TK * KB;   // first byte of the second scatter tile
 #pragma unroll
-  for (int j = 0; j < KCPT; ++j) {
+  for (int j = 0; j < 2 * KCPT; ++j) {
     const unsigned c = threadIdx.x + j * NT;
     if (c < nwc) {
       const uint4 q = sw[c];
@@ -926,7 +939,8 @@ __device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *__
           C k = key_at<KB>(q, v);
           if (RAW) k = encode<KB>(k, a.codec);
           const unsigned bk = cl(k);
-          atomicAdd(&s_hist[bk], 1u);
+          unsigned *h = j < KCPT - 1 ? h0 : j >= KCPT ? h1 : (off < split ? h0 : h1);
+          atomicAdd(&h[bk], 1u);
           ids[(off - lo) / KB] = (unsigned char)bk;   // for the scatter pass
         }
       }
@@ -961,7 +975,6 @@ __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *
 #pragma unroll
     for (unsigned v = 0; v < V; ++v) pk[j * V + v] = ~0u;
     if (c < nwc) {
-      const uint4 q = sw[c];
       const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
 #pragma unroll
       for (unsigned v = 0; v < V; ++v) {
@@ -1089,9 +1102,12 @@ __device__ __forceinline__ void load_desc(const SortArgs &a, unsigned long long 
   for (int k = 0; k < 8; ++k) sw[k] = w[k];
 }
 
-// Keys per tile of a range.
-__device__ __forceinline__ unsigned tile_keys_of(const SortArgs &a, const SegDesc &seg) {
-  return (seg.flags & SEG_KWAY) ? a.kw_tile_keys : a.tile_keys;
+// Keys per tile of a range's item: K-way counting tiles cover two scatter
+// tiles.
+__device__ __forceinline__ unsigned tile_keys_of(const SortArgs &a, const SegDesc &seg,
+                                                 unsigned long long item) {
+  if (!(seg.flags & SEG_KWAY)) return a.tile_keys;
+  return (item & ITEM_PHASE) ? a.kw_tile_keys : 2 * a.kw_tile_keys;
 }
 
 // Starts the TMA bulk copy of the tile's 16-byte-aligned window into `buf`.
@@ -1102,7 +1118,7 @@ __device__ __forceinline__ unsigned tile_keys_of(const SortArgs &a, const SegDes
 template <int KB, int CPT>
 __device__ __forceinline__ void issue_tile(const SortArgs &a, unsigned long long item, const SegDesc &seg,
                                            unsigned char *buf, uint64_t *bar) {
-  const unsigned T = tile_keys_of(a, seg);
+  const unsigned T = tile_keys_of(a, seg, item);
   const unsigned i = (unsigned)(item & ITEM_INDEX);
   const uint64_t b = seg.begin, e = seg.end;
   const bool par = seg.flags & SEG_PARITY;
@@ -1170,6 +1186,8 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
   constexpr unsigned TKW = kw_tile_keys(KB, CPT);
   constexpr unsigned RS = kw_sample_r<KB, CPT>();
   static_assert(kw_scratch_bytes<KB, RS>() <= (unsigned)part_window(CPT), "setup sample fits the window");
+  static_assert(2 * TKW * KB + 32 <= (unsigned)part_window(CPT), "a counting tile fits the window");
+  static_assert(NT == KW_MAX, "one thread per bucket");
   constexpr unsigned PIV_BYTES = SAMPLE * sizeof(C) + SAMPLE / (64 / KB) * 8;
   constexpr unsigned LOOKUP_BYTES = KW_MAX * sizeof(C) + KW_TABLE * 2;
   constexpr unsigned AUX = PIV_BYTES > LOOKUP_BYTES ? PIV_BYTES : LOOKUP_BYTES;
@@ -1196,7 +1214,10 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
   M *stage = (M *)(smem + part_window(CPT) / 2);
 
   const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (unsigned j = tid; j < KW_MAX; j += NT) s_hist[j] = 0;
+  for (unsigned j = tid; j < KW_MAX; j += NT) {
+    s_hist[j] = 0;
+    s_off[j] = 0;
+  }
   if (blockIdx.x == 0 && tid == 0) a.hdr->part_grid = gridDim.x;
   if (tid == 0) {
     mbar_init(&s_bar, 1);
@@ -1296,7 +1317,7 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
     }
 
     const bool phase1 = (item & ITEM_PHASE) != 0;
-    const unsigned T = kway ? TKW : a.tile_keys;
+    const unsigned T = kway ? (phase1 ? TKW : 2 * TKW) : a.tile_keys;
     const uint64_t b = sg.begin, e = sg.end;
     const bool par = sg.flags & SEG_PARITY, raw = sg.flags & SEG_RAW;
     const unsigned char *src = (const unsigned char *)(par ? a.alt : a.keys);
@@ -1321,13 +1342,16 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
       cl.sk = s_split[s_nsp];
       cl.sh = s_shift;
       if (!phase1) {
-        if (raw) kw_count_tile<KB, KCPT, true>(a, sw, nwc, lo, hi, cl, s_hist, a.kw_ids + t0);
-        else kw_count_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, cl, s_hist, a.kw_ids + t0);
+        // s_off (free outside a scatter tile) holds the second histogram
+        if (raw) kw_count_tile<KB, KCPT, true>(a, sw, nwc, lo, hi, cl, s_hist, s_off, a.kw_ids + t0);
+        else kw_count_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, cl, s_hist, s_off, a.kw_ids + t0);
         __syncthreads();
-        if (tid < K) {
-          const unsigned x = s_hist[tid];
-          if (x) atomicAdd(&kw.cnt[i % KW_STRIPES][tid], x);
+        if (tid < K) {   // each half counts for the stripe of its scatter tile, 2i or 2i + 1
+          const unsigned x0 = s_hist[tid], x1 = s_off[tid];
+          if (x0) atomicAdd(&kw.cnt[(2 * i) % KW_STRIPES][tid], x0);
+          if (x1) atomicAdd(&kw.cnt[(2 * i + 1) % KW_STRIPES][tid], x1);
           s_hist[tid] = 0;
+          s_off[tid] = 0;
         }
       } else {
         const unsigned char *s_ids =
@@ -1341,10 +1365,13 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
       }
       fence_proxy_async_smem();   // the next TMA copy reuses the window
       __syncthreads();
+      // a scatter tile leaves its bucket offsets in s_off: clear them for the
+      // next counting tile (ordered before it by the barrier after the claim)
+      if (phase1) s_off[tid] = 0;
       if (tid == 0) {
         pend_prev = atom_add_release(&a.segs[sid].tiles_done, 1u);
         pend_sid = sid;
-        pend_nt = sg.ntiles;
+        pend_nt = phase1 ? sg.ntiles : kw_count_items(sg.ntiles);
         pend_phase = phase1;
       }
       continue;
