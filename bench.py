@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -114,6 +115,23 @@ def alu_peak(clk):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     return sms * 4 * 16 * mhz * 1e6, f"derived: {sms} SMs x 4 sub-partitions x 16 ALU lanes x {mhz:.0f} MHz"
+
+
+# Nominal HBM3e bandwidth of one GB300 (the measured copy bandwidth is the
+# main denominator; this one is reported beside it).
+NOMINAL_HBM_GBS = 8000.0
+# Leaf cutoff the library uses by key size when none is set.
+DEFAULT_LEAF_CUTOFF = {2: 4096, 4: 4096, 8: 8192, 16: 4096}
+
+
+def ideal_two_way(kb: int, n: int, cutoff: int) -> dict:
+    """Bytes of an ideal two-way Quicksort of n keys: every level halves every
+    range exactly, so ceil(log2(n / cutoff)) partition levels and one leaf
+    pass each read and write all n keys. A bad pivot cannot inflate the
+    fraction measured against this (the levels are not the ones run), and
+    K-way levels can beat it."""
+    levels = max(0, math.ceil(math.log2(n / cutoff))) if n > cutoff else 0
+    return {"bytes": 2 * n * kb * (levels + 1), "partition_levels": levels, "leaf_cutoff": cutoff}
 
 
 def hbm_peak():
@@ -543,6 +561,7 @@ def run_gpu(args):
     traffic = recorded_traffic(f"{args.dtype}:{args.n}:{args.dist}", KERNEL_SOURCES)
     leaf_ms = sum(v["ms"] for k, v in prof.items() if k.startswith("leaf")) / args.steps
     sort_bytes = part_bytes + 2 * kb * args.n
+    ideal = ideal_two_way(kb, args.n, vq.get_option("leaf_cutoff") or DEFAULT_LEAF_CUTOFF[kb])
     kernels = {k: {"ms_per_launch": v["ms"] / max(1, v["launches"]), "launches": v["launches"]}
                for k, v in prof.items()}
     gpu_launches = sum(v["launches"] for v in prof.values())
@@ -552,7 +571,7 @@ def run_gpu(args):
     # alternate between two streams (vqsort_sort_host_async), so one array
     # uploads while the other sorts and writes back over the other direction
     # of the host link. The single synchronous call is reported beside it.
-    e2e_val = e2e_single = None
+    e2e_val = e2e_single = e2e_link = None
     if not args.no_e2e:
         steps = max(2, args.e2e_steps)
         streams = [torch.cuda.Stream(), torch.cuda.Stream()]
@@ -585,7 +604,28 @@ def run_gpu(args):
         t0 = time.perf_counter()
         vq.sort_host(views[0], args.dtype)
         e2e_single = world * args.n / (time.perf_counter() - t0) / 1e9
-        del bufs, views
+        # the host link of this machine (plain pinned copies of the same size,
+        # best of three), to read the end-to-end numbers against
+        dev = torch.empty(bufs[0].numel(), dtype=torch.uint8, device=f"cuda:{local}")
+
+        def copy_ms(dst, srcb):
+            best = float("inf")
+            for _ in range(3):
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                c0.record()
+                dst.copy_(srcb, non_blocking=True)
+                c1.record()
+                c1.synchronize()
+                best = min(best, c0.elapsed_time(c1))
+            return best
+
+        h2d_ms, d2h_ms = copy_ms(dev, bufs[0]), copy_ms(bufs[0], dev)
+        nbytes = bufs[0].numel()
+        e2e_link = {"h2d_gbs": nbytes / h2d_ms / 1e6, "d2h_gbs": nbytes / d2h_ms / 1e6,
+                    "copy_only_gkeys_per_s": args.n / ((h2d_ms + d2h_ms) * 1e-3) / 1e9,
+                    "how": "one pinned array up, then down, no sort (CUDA events, best of 3)"}
+        del dev, bufs, views
 
     line = {
         "metric": METRIC,
@@ -604,6 +644,10 @@ def run_gpu(args):
         "sort_roofline": {"bytes_per_step": sort_bytes,
                           "achieved_gbs": sort_bytes / (ms_step * 1e-3) / 1e9,
                           "frac": sort_bytes / (ms_step * 1e-3) / 1e9 / peak,
+                          "frac_nominal": sort_bytes / (ms_step * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
+                          "ideal_two_way": dict(ideal, ms_at_peak=ideal["bytes"] / peak / 1e6,
+                                                frac=ideal["bytes"] / peak / 1e6 / ms_step,
+                                                frac_nominal=ideal["bytes"] / NOMINAL_HBM_GBS / 1e6 / ms_step),
                           "levels_run_keys": st["keys_partitioned"], "keys_counted": st["keys_counted"],
                           "kway_ranges": st["kway_ranges"], "max_depth": st["max_depth"],
                           "leaf_ms_per_step": leaf_ms},
@@ -614,7 +658,8 @@ def run_gpu(args):
                 "d2h_bytes_per_step": args.n * kb,
                 "path": "vqsort_sort_host_async, one pinned host array per step, steps alternating over two "
                         "streams (upload, sort and write-back of every step inside the timed region)",
-                "single_call": e2e_single, "single_call_path": "vqsort_sort_host (one array, waits)"},
+                "single_call": e2e_single, "single_call_path": "vqsort_sort_host (one array, waits)",
+                "link": e2e_link},
         "clocks": clk,
     }
     # the leaf networks: compare-exchanges (counted on the device) x integer

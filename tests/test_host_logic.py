@@ -85,3 +85,39 @@ def test_bench_takes_max_over_two_gloo_ranks():
         assert p.exitcode == 0
     res = dict(q.get(timeout=10) for _ in range(2))
     assert res == {0: 11.0, 1: 11.0}
+
+
+def test_ideal_two_way_roofline():
+    import bench
+    # 1e8 u64 keys, cutoff 8192: ceil(log2(12207.03)) = 14 levels + the leaf pass
+    r = bench.ideal_two_way(8, 10**8, 8192)
+    assert r["partition_levels"] == 14 and r["bytes"] == 2 * 10**8 * 8 * 15
+    # exactly a power of two above the cutoff: 2^20 / 2^12 needs 8 halvings
+    assert bench.ideal_two_way(4, 1 << 20, 4096)["partition_levels"] == 8
+    # one leaf only
+    assert bench.ideal_two_way(2, 4096, 4096) == {"bytes": 2 * 4096 * 2, "partition_levels": 0,
+                                                   "leaf_cutoff": 4096}
+
+
+def test_bench_default_cutoffs_match_library():
+    """The bench's copy of the per-key-size default leaf cutoff agrees with
+    the library's rule in launch.h."""
+    import re
+    import bench
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_2205_05982_gb300", "csrc", "launch.h")).read()
+    body = re.search(r"default_leaf_cutoff\(int kb\) \{\s*return ([^;]+);", src).group(1)
+    expr = re.sub(r"(\d+)u\b", r"\1", body)
+
+    def lib(kb):
+        # the body is a chain of `kb == K ? V : ...` conditionals
+        e = expr
+        while "?" in e:
+            m = re.match(r"\s*kb == (\d+) \? (\d+) : (.*)", e, re.S)
+            if int(m.group(1)) == kb:
+                return int(m.group(2))
+            e = m.group(3)
+        return int(e)
+
+    for kb in (2, 4, 8, 16):
+        assert bench.DEFAULT_LEAF_CUTOFF[kb] == lib(kb)
