@@ -282,11 +282,11 @@ def bits_view(t, torch):
     return t.view({2: torch.int16, 4: torch.int32, 8: torch.int64}[t.element_size()])
 
 
-def time_sorts(vq, torch, copies, ws, dtype, warmup):
+def time_sorts(vq, torch, copies, ws, dtype, warmup, descending=False):
     """Sorts copies[0:warmup] untimed, then each remaining copy; returns
     (ms per sort, stats of the last sort, per-kernel profile)."""
     for i in range(warmup):
-        vq.sort_ws_(copies[i], ws, dtype)
+        vq.sort_ws_(copies[i], ws, dtype, descending=descending)
     torch.cuda.synchronize()
     vq.profile_reset()
     vq.profile_enable(True)
@@ -294,7 +294,7 @@ def time_sorts(vq, torch, copies, ws, dtype, warmup):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for c in copies[warmup:]:
-        vq.sort_ws_(c, ws, dtype)
+        vq.sort_ws_(c, ws, dtype, descending=descending)
     e1.record()
     torch.cuda.synchronize()
     vq.profile_enable(False)
@@ -321,6 +321,40 @@ def extra_dtypes(vq, torch, peak, n):
                    "sort_frac": (pb + 2 * kb * n) / (ms * 1e-3) / 1e9 / peak,
                    "max_depth": st["max_depth"]}
         del copies, src, ws
+        torch.cuda.empty_cache()
+    return out
+
+
+DISTRIBUTIONS = ("uniform", "distinct16", "equal", "sorted", "reverse", "organpipe")
+
+
+def extra_distributions(vq, torch, n):
+    """The 48 runs of the 1e8-keys-per-dtype workload: u64, f32, i32 and i16
+    keys in six distributions (uniform, 16 distinct values, all equal,
+    sorted, reverse sorted, organ pipe), each sorted ascending and
+    descending; GKeys/s over two timed sorts after one warm-up."""
+    out = {}
+    for dt in ("u64", "f32", "i32", "i16"):
+        ws = vq.alloc_workspace(dt, n)
+        srt = None
+        for dist in DISTRIBUTIONS:
+            if dist == "reverse":   # the sorted array backwards (as the generator makes it)
+                src = torch.flip(srt, [0]).contiguous()
+                srt = None
+            else:
+                src = to_device_bits(inputs.make(dt, n, dist, specials=dt == "f32"), dt, torch)
+                if dist == "sorted":
+                    srt = src.clone()
+            for desc in (False, True):
+                copies = [src.clone() for _ in range(3)]
+                ms, st, _ = time_sorts(vq, torch, copies, ws, dt, 1, descending=desc)
+                assert st["device_status"] == 0, (dt, dist, desc, st)
+                out[f"{dt}:{dist}:{'desc' if desc else 'asc'}"] = {
+                    "gkeys_per_s": n / (ms * 1e-3) / 1e9, "ms": ms, "max_depth": st["max_depth"],
+                    "fallback_keys": st["fallback_keys"], "equal_keys": st["equal_keys"]}
+                del copies
+            del src
+        del ws
         torch.cuda.empty_cache()
     return out
 
@@ -620,11 +654,18 @@ def run_gpu(args):
                 best = min(best, c0.elapsed_time(c1))
             return best
 
-        h2d_ms, d2h_ms = copy_ms(dev, bufs[0]), copy_ms(bufs[0], dev)
+        # every array of the timed loop: host sorts of different pinned
+        # arrays of one process were measured at very different rates
+        h2d_ms = [copy_ms(dev, b) for b in bufs]
+        d2h_ms = [copy_ms(b, dev) for b in bufs]
         nbytes = bufs[0].numel()
-        e2e_link = {"h2d_gbs": nbytes / h2d_ms / 1e6, "d2h_gbs": nbytes / d2h_ms / 1e6,
-                    "copy_only_gkeys_per_s": args.n / ((h2d_ms + d2h_ms) * 1e-3) / 1e9,
-                    "how": "one pinned array up, then down, no sort (CUDA events, best of 3)"}
+        h2d_med, d2h_med = statistics.median(h2d_ms), statistics.median(d2h_ms)
+        e2e_link = {"h2d_gbs": nbytes / h2d_med / 1e6, "d2h_gbs": nbytes / d2h_med / 1e6,
+                    "copy_only_gkeys_per_s": args.n / ((h2d_med + d2h_med) * 1e-3) / 1e9,
+                    "per_array_h2d_gbs": [round(nbytes / t / 1e6, 1) for t in h2d_ms],
+                    "per_array_d2h_gbs": [round(nbytes / t / 1e6, 1) for t in d2h_ms],
+                    "how": "each pinned array of the timed loop up, then down, no sort (CUDA events, "
+                           "best of 3 per array; the scalar rates are the medians)"}
         del dev, bufs, views
 
     line = {
@@ -680,6 +721,7 @@ def run_gpu(args):
             del src
             torch.cuda.empty_cache()
             line["per_dtype"] = extra_dtypes(vq, torch, peak, args.n)
+            line["distributions"] = extra_distributions(vq, torch, args.n)
             line["wide"] = extra_wide(vq, torch, peak)
             line["partition_sweep"] = extra_partition_sweep(vq, torch, peak)
             line["stable"] = extra_stable(vq, torch, args.n)

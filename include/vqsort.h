@@ -121,7 +121,8 @@ vq_status vqsort_sort_segmented_ws(vq_dtype dt, void *d_keys, size_t n_total,
    waits. Uses a library-owned stream and device buffer on the current
    device. If h_keys is pinned (page-locked and mapped), the leaf kernels
    write the sorted keys straight into it, so the download overlaps the
-   leaves' work; pageable memory is copied back after the sort. */
+   leaves' work (VQ_OPT_HOST_DIRECT = 0: copied back after the sort);
+   pageable memory is copied back after the sort. */
 vq_status vqsort_sort_host(vq_dtype dt, void *h_keys, size_t n, int ascending);
 
 /* The same end-to-end sort of a HOST array, enqueued on `stream` without
@@ -239,12 +240,16 @@ typedef enum vq_option {
                                256, 512 or 1024: that many threads when they hold a
                                cutoff-size leaf at 16 keys each (else cutoff/16); 16-byte
                                keys: 256 or (otherwise) 512 threads */
-  VQ_OPT_KWAY = 7           /* 1 (default): ranges of at least 4x the leaf cutoff are split
+  VQ_OPT_KWAY = 7,          /* 1 (default): ranges of at least 4x the leaf cutoff are split
                                into 16..256 buckets per level (sampled splitters, a counting
                                pass and a scatter pass; the K > 2 partition of Sec. 4.2),
                                with equality buckets when the splitters repeat; 0: every
                                level is the paper's two-way Partition. The output is the
                                same. */
+  VQ_OPT_HOST_DIRECT = 8    /* host-array sorts of pinned memory: 1 (default): the leaf
+                               kernels store the result straight into the pinned array, so
+                               the download overlaps the leaves; 0: a copy engine copies it
+                               back after the sort. The output is the same. */
 } vq_option;
 vq_status vqsort_set_option(vq_option opt, int64_t value);
 int64_t vqsort_get_option(vq_option opt);

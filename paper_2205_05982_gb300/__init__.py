@@ -30,7 +30,7 @@ KEY_BYTES = {"i16": 2, "u16": 2, "i32": 4, "u32": 4, "f32": 4, "i64": 8, "u64": 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported device", 3: "out of memory",
           4: "CUDA error", 5: "timeout", 6: "internal capacity overflow"}
 OPTIONS = {"depth_limit": 0, "leaf_cutoff": 1, "seed": 2, "spin_limit": 3, "test_stall": 4,
-           "tile_bytes": 5, "leaf_threads": 6, "kway": 7}
+           "tile_bytes": 5, "leaf_threads": 6, "kway": 7, "host_direct": 8}
 
 
 class VqError(RuntimeError):

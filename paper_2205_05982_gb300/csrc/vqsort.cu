@@ -55,6 +55,7 @@ int64_t g_test_stall = 0;
 int64_t g_tile_bytes = 0;     // 0: by key size (tile_cpt)
 int64_t g_leaf_threads = 0;   // 0: 16 keys per thread at the cutoff
 int64_t g_kway = 1;           // K-way levels for ranges of >= 4 x the leaf cutoff
+int64_t g_host_direct = 1;    // host sorts: leaves store into pinned host arrays
 
 // 16-byte chunks per thread of a partition tile window. Default: 64 KiB
 // windows (3 blocks per SM) for 8- and 16-byte keys, 32 KiB (5 per SM) for
@@ -414,18 +415,21 @@ vq_status host_enqueue(vq_dtype dt, void *h_keys, size_t n, int ascending, cudaS
     }
     dbuf = b.ptr;
   }
-  void *h_dev = nullptr;
-  cudaPointerAttributes attr{};
-  if (cudaPointerGetAttributes(&attr, h_keys) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
-      attr.devicePointer)
-    h_dev = attr.devicePointer;
-  cudaGetLastError();
-  if (cudaMemcpyAsync(dbuf, h_keys, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return VQ_ERR_CUDA;
-  int64_t dl;
+  int64_t dl, direct;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     dl = g_depth_limit;
+    direct = g_host_direct;
   }
+  // a pinned array is written by the leaves themselves (unless the option
+  // asks for a copy back), so its download overlaps their work
+  void *h_dev = nullptr;
+  cudaPointerAttributes attr{};
+  if (direct && cudaPointerGetAttributes(&attr, h_keys) == cudaSuccess &&
+      attr.type == cudaMemoryTypeHost && attr.devicePointer)
+    h_dev = attr.devicePointer;
+  cudaGetLastError();
+  if (cudaMemcpyAsync(dbuf, h_keys, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return VQ_ERR_CUDA;
   const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb), dl, true, tile_cpt(kb));
   void *ws;
   size_t wsb;
@@ -652,6 +656,7 @@ vq_status vqsort_set_option(vq_option opt, int64_t value) {
       g_leaf_threads = value;
       return VQ_OK;
     case VQ_OPT_KWAY: g_kway = value ? 1 : 0; return VQ_OK;
+    case VQ_OPT_HOST_DIRECT: g_host_direct = value ? 1 : 0; return VQ_OK;
   }
   return VQ_ERR_INVALID;
 }
@@ -667,6 +672,7 @@ int64_t vqsort_get_option(vq_option opt) {
     case VQ_OPT_TILE_BYTES: return g_tile_bytes;
     case VQ_OPT_LEAF_THREADS: return g_leaf_threads;
     case VQ_OPT_KWAY: return g_kway;
+    case VQ_OPT_HOST_DIRECT: return g_host_direct;
   }
   return -1;
 }

@@ -248,18 +248,24 @@ def pinned_like(a):
     ("u128", 500_009, "uniform"), ("kv64", 300_007, "uniform"), ("u32", 100_000, "equal"),
     ("u64", 1, "uniform"), ("f64", 5000, "uniform")])
 @pytest.mark.parametrize("ascending", (True, False))
-def test_host_entry_pinned(vq, oracle_mod, dtype, n, dist, ascending):
-    """Pinned host buffers are written by the leaf kernels directly."""
+@pytest.mark.parametrize("direct", (0, 1))
+def test_host_entry_pinned(vq, oracle_mod, dtype, n, dist, ascending, direct):
+    """Pinned host buffers: written by the leaf kernels directly (default),
+    or copied back after the sort (host_direct = 0)."""
     a = make(dtype, n, dist, seed=n % 101)
     want = oracle_mod.sort(a, dtype, ascending)
     keep, b = pinned_like(a)
-    vq.sort_host(b, dtype, descending=not ascending)
+    vq.set_option("host_direct", direct)
+    try:
+        vq.sort_host(b, dtype, descending=not ascending)
+    finally:
+        vq.set_option("host_direct", 1)
     assert same_bits(b, want)
 
 
 @pytest.mark.parametrize("limit", (0, 2))
 def test_host_entry_pinned_fallback(vq, oracle_mod, limit):
-    """The depth-bound merge fallback writes the pinned buffer too."""
+    """The depth-bound merge fallback writes the pinned buffer directly too."""
     a = make("u64", 200_003, "uniform", seed=3)
     want = oracle_mod.sort(a, "u64", True)
     vq.set_option("depth_limit", limit)
@@ -439,10 +445,19 @@ def test_beyond_2_pow_31_keys(vq, ascending):
     torch.cuda.empty_cache()
 
 
-def test_host_async_two_streams(vq, oracle_mod):
+@pytest.mark.parametrize("direct", (0, 1))
+def test_host_async_two_streams(vq, oracle_mod, direct):
     """Several host arrays, pinned and pageable, sorted on two streams at
     once: each ends up equal to the oracle's sort."""
     import torch
+    vq.set_option("host_direct", direct)
+    try:
+        _host_async_two_streams(vq, oracle_mod, torch)
+    finally:
+        vq.set_option("host_direct", 1)
+
+
+def _host_async_two_streams(vq, oracle_mod, torch):
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     cases = [("u64", 3_000_017, True), ("f32", 2_000_003, False), ("i16", 1_000_001, True),
              ("u64", 2_500_001, False), ("kv64", 300_007, True)]
