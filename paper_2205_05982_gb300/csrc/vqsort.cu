@@ -93,8 +93,10 @@ Layout make_layout(int kb, uint64_t n, uint64_t S, unsigned C, int64_t depth_lim
   const uint64_t per_level = n / (C + 1ull) + 1;
   Layout L{};
   const uint64_t cap_segs = (levels + 1) * per_level + 16;
-  // Per level: a K-way range runs its (smaller) tiles twice, counting and
-  // scattering; every range may add a partial tile per pass and one setup item.
+  // Per level: a K-way range runs its scatter tiles (T_K keys, half a
+  // window) and half as many counting tiles, bounded here by two passes of
+  // scatter tiles; every range may add a partial tile per pass and one setup
+  // item.
   const uint64_t TK = kw_tile_keys(kb, cpt);
   const uint64_t cap_q = (levels + 1) * (2 * (n / TK + 1) + 3 * per_level) + 2 * S + 16;
   // K-way records: ranges of >= 4C keys; when they run out, ranges are split
