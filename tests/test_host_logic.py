@@ -121,3 +121,34 @@ def test_bench_default_cutoffs_match_library():
 
     for kb in (2, 4, 8, 16):
         assert bench.DEFAULT_LEAF_CUTOFF[kb] == lib(kb)
+
+
+def test_reference_sample_is_bounded():
+    import bench
+    assert bench.reference_sample_keys(10**8, 10, 3) == 10_000_000        # capped at 1e7
+    assert bench.reference_sample_keys(10**8, 1000, 3) == int(bench.REFERENCE_SECONDS *
+                                                              bench.ORACLE_KEYS_PER_S / 1003)
+    assert bench.reference_sample_keys(10**8, 10**6, 0) == 100_000        # floor
+    assert bench.reference_sample_keys(5000, 10, 3) == 5000               # never above n
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference: one JSON line with the reference arm's
+    keys, timing the oracle on the host for exactly --steps steps."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--n", "300000", "--steps", "2", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
+    assert d["value"] > 0 and d["unit"] == "GKeys/s" and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GKeys/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
