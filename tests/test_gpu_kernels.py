@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2205_05982_gb300 import inputs
-from tests.gpu_util import same_bits, to_dev, to_host
+from tests.gpu_util import to_dev, to_host
 from tests.total_order import bit_rows
 
 pytestmark = pytest.mark.gpu
