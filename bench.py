@@ -183,9 +183,9 @@ def cpu_baseline(args, a, seconds):
     }
 
 
-# Keys per second the oracle sorts on one host core of the GPU machines (u64,
-# 1e7 keys: 0.016 GKeys/s); sizes the reference arm's per-step sample so that
-# its warm-up and timed steps together take about REFERENCE_SECONDS.
+# Keys per second the oracle sorts on one Grace core (u64, 1e7 keys: 0.016
+# GKeys/s); sizes the reference arm's per-step sample so that its warm-up and
+# timed steps together take about REFERENCE_SECONDS.
 ORACLE_KEYS_PER_S = 16e6
 REFERENCE_SECONDS = 90.0
 
