@@ -298,8 +298,9 @@ struct Header {
   unsigned long long part_grid;    // blocks of the partition kernel (statistics)
   unsigned long long n_leaf_mid, cur_leaf_mid;   // mid-size leaf list
   unsigned long long leaves_mid;   // (statistics)
-  unsigned long long leaf_ce;      // compare-exchanges run by the leaf networks (statistics)
-  unsigned long long pad[6];
+  unsigned long long leaf_ce;      // key comparisons of the leaf sorts (statistics)
+  unsigned long long leaf_keys_warp, leaf_keys_mid, leaf_keys_block;   // keys per leaf list (statistics)
+  unsigned long long pad[3];
 };
 static_assert(sizeof(Header) % 64 == 0, "header size");
 

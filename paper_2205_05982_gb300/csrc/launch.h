@@ -31,13 +31,12 @@ __host__ __device__ constexpr unsigned kw_tile_keys(int kb, int cpt = PART_CPT) 
 }
 
 // Mid-size leaves (more than a warp leaf, at most MID_NT * 16 keys; 16-byte
-// keys: MID_NT * 8) are sorted by MID_NT threads holding up to 16 keys
-// each, which keeps more network steps inside a thread's registers. Measured
-// on 1e8-key sorts this pays for 2- and 4-byte keys (codes in one register)
-// and not for 8-byte keys, whose mid-size ranges stay with the block leaves.
+// keys: MID_NT * 8) are sorted by MID_NT threads holding 8 or 16 keys each:
+// many small blocks per SM, and every thread's merge-path search shared by
+// as many keys as its registers hold.
 constexpr int MID_NT = 128;
 __host__ __device__ constexpr unsigned mid_max_keys(int kb) { return kb == 16 ? MID_NT * 8u : MID_NT * 16u; }
-__host__ __device__ constexpr unsigned mid_leaf_limit(int kb) { return kb == 8 ? 0u : mid_max_keys(kb); }
+__host__ __device__ constexpr unsigned mid_leaf_limit(int kb) { return mid_max_keys(kb); }
 
 constexpr int LEAF_NT = 1024;       // threads of the block leaf kernel
 constexpr int FB_NT = 256;          // threads of the merge fallback kernel
@@ -66,8 +65,22 @@ __host__ __device__ constexpr unsigned max_leaf_cutoff(int kb) {
   return kb <= 8 ? 16384u : 4096u;   // 16-byte keys: at most 4 per thread in registers
 }
 __host__ constexpr unsigned code_bytes(int kb) { return kb == 2 ? 4u : (unsigned)kb; }
-__host__ constexpr size_t leaf_block_smem(int kb, unsigned cutoff) {
-  return (size_t)(cutoff + cutoff / 32) * code_bytes(kb);
+
+// Keys per thread for a leaf of len keys on nt threads: the fewest of 4, 8
+// and 16 (at most rmax) that hold it, so that as many threads as possible
+// share the work.
+__host__ __device__ constexpr int leaf_r_for(unsigned len, int nt, int rmax) {
+  return len <= 4u * (unsigned)nt || rmax <= 4 ? 4 : len <= 8u * (unsigned)nt || rmax <= 8 ? 8 : 16;
+}
+// Most keys per thread of a block leaf on nt threads: 16, or fewer when the
+// largest cutoff of the key size needs fewer (16-byte keys: 4096 / nt).
+__host__ __device__ constexpr int leaf_rmax(int kb, int nt) {
+  return (int)max_leaf_cutoff(kb) / nt < 16 ? (int)max_leaf_cutoff(kb) / nt : 16;
+}
+// Shared memory of a block leaf on nt threads for leaves of up to `cutoff`
+// keys: R keys per thread plus one spare slot per thread (bank spread).
+__host__ constexpr size_t leaf_block_smem(int kb, unsigned cutoff, int nt) {
+  return (size_t)nt * (leaf_r_for(cutoff, nt, leaf_rmax(kb, nt)) + 1) * code_bytes(kb);
 }
 
 cudaError_t launch_prep(const SortArgs &a, cudaStream_t s);

@@ -85,48 +85,64 @@ template <int KB> __global__ void __launch_bounds__(256) k_leaf_warp(SortArgs a)
   }
 }
 
+// Runs the register networks build before merge-path rounds take over. A
+// bitonic phase joining runs of L keys costs log2(2L) steps of a shuffle and
+// a compare-and-select per key; a merge round costs about twenty
+// instructions per output key for 64-bit codes plus a binary search per
+// thread (about a dozen probes, shared by its R keys). The phases stay in
+// registers while they are the cheaper of the two: longest for 32-bit codes
+// (one min or max instruction per exchange), shortest for 128-bit codes,
+// and longer with fewer keys per thread (the search is shared by fewer).
+template <int KB, int R> __host__ __device__ constexpr unsigned leaf_run0() {
+  return KB <= 4 ? 256u : KB == 8 ? (R >= 16 ? 64u : 128u) : (R >= 8 ? 32u : 64u);
+}
+
+// NT threads sort one range of len <= NT*R keys: the first ns/R threads load
+// the keys (coalesced; ns = len rounded up to the register-stage run),
+// padded with the all-ones code, the last value in sort order (Sec. 2.3);
+// merge_sort_block sorts them; the result is staged in shared memory and
+// stored decoded, coalesced.
 template <int KB, int R, int NT>
 __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, uint64_t b, unsigned len, bool raw,
                                            typename KT<KB>::Code *sx) {
   using C = typename KT<KB>::Code;
+  constexpr unsigned L0 = leaf_run0<KB, R>() < 32u * R ? leaf_run0<KB, R>() : 32u * R;
   const unsigned t = threadIdx.x;
+  const unsigned ns = (len + L0 - 1) / L0 * L0;
+  const unsigned nta = ns / R;
   C k[R];
+  if (t < nta) {
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const unsigned j = r * NT + t;
-    if (j < len) {
-      C c = load_key<KB>(src, b + j);
-      k[r] = raw ? encode<KB>(c, a.codec) : c;
-    } else {
-      k[r] = KT<KB>::max_code();
+    for (int r = 0; r < R; ++r) {
+      const unsigned j = r * nta + t;
+      if (j < len) {
+        C c = load_key<KB>(src, b + j);
+        k[r] = raw ? encode<KB>(c, a.codec) : c;
+      } else {
+        k[r] = KT<KB>::max_code();
+      }
     }
-  }
-  group_sort<C, R, NT>(k, t, sx);
-  // stage in shared memory (one pad slot per 32 keys) for coalesced stores
+  } else {
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const unsigned i = t * R + r;
-    sx[i + (i >> 5)] = k[r];
+    for (int r = 0; r < R; ++r) k[r] = KT<KB>::max_code();
+  }
+  merge_sort_block<C, R, NT, L0>(k, t, ns, sx);
+  if (t < nta) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) sx[spad<R>(t * R + r)] = k[r];
   }
   __syncthreads();
   const C *__restrict__ st = sx;
 #pragma unroll 4
-  for (unsigned j = t; j < len; j += NT) store_key<KB>(a.out, b + j, decode<KB>(st[j + (j >> 5)], a.codec));
-  if (t == 0) atomicAdd(&a.hdr->leaf_ce, network_ce<NT, R>());
+  for (unsigned j = t; j < len; j += NT) store_key<KB>(a.out, b + j, decode<KB>(st[spad<R>(j)], a.codec));
+  if (t == 0) atomicAdd(&a.hdr->leaf_ce, merge_sort_cmps<R, NT, L0>(ns));
   __syncthreads();
 }
 
-// Most keys per thread of a block leaf: 16, or fewer when the largest
-// cutoff of the key size needs fewer (16-byte keys: 4096 / NT).
-template <int KB, int NT> __host__ __device__ constexpr int leaf_rmax() {
-  return (int)max_leaf_cutoff(KB) / NT < 16 ? (int)max_leaf_cutoff(KB) / NT : 16;
-}
-
-// NT threads sort one range of up to RMAX*NT keys, R = P/NT keys per thread
-// where P is the range length rounded up to a power of two (>= NT).
+// NT threads sort one range of up to RMAX*NT keys at a time.
 template <int KB, int NT>
 __global__ void __launch_bounds__(NT, NT <= 256 && KB <= 8 ? 4 : NT <= 512 ? 2 : 1) k_leaf_block(SortArgs a) {
-  constexpr int RMAX = leaf_rmax<KB, NT>();
+  constexpr int RMAX = leaf_rmax(KB, NT);
   using C = typename KT<KB>::Code;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_idx;
@@ -140,7 +156,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 && KB <= 8 ? 4 : NT <= 512 ? 2 :
     __syncthreads();
     if (idx >= n) break;
     const LeafEntry le = a.leaf_block[idx];
-    if (le.begin + le.len > a.n_total || le.len > (unsigned)(RMAX * NT)) {   // guard
+    // guard: inside the array, and no longer than the cutoff the shared
+    // memory was sized for
+    if (le.begin + le.len > a.n_total || le.len > (unsigned)(RMAX * NT) ||
+        le.len > (a.leaf_cutoff < 1024 ? 1024u : a.leaf_cutoff)) {
       if (threadIdx.x == 0) guard_failed(a, GUARD_LEAF);
       continue;
     }
@@ -154,11 +173,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 && KB <= 8 ? 4 : NT <= 512 ? 2 :
       }
       continue;
     }
-    if (len <= NT) block_leaf<KB, 1, NT>(a, src, le.begin, len, raw, sx);
-    else if (len <= 2 * NT) block_leaf<KB, 2, NT>(a, src, le.begin, len, raw, sx);
-    else if (len <= 4 * NT || RMAX <= 4) block_leaf<KB, (RMAX < 4 ? RMAX : 4), NT>(a, src, le.begin, len, raw, sx);
-    else if (len <= 8 * NT || RMAX <= 8) block_leaf<KB, (RMAX < 8 ? RMAX : 8), NT>(a, src, le.begin, len, raw, sx);
-    else block_leaf<KB, RMAX, NT>(a, src, le.begin, len, raw, sx);
+    switch (leaf_r_for(len, NT, RMAX)) {
+      case 4: block_leaf<KB, 4, NT>(a, src, le.begin, len, raw, sx); break;
+      case 8: block_leaf<KB, (RMAX < 8 ? RMAX : 8), NT>(a, src, le.begin, len, raw, sx); break;
+      default: block_leaf<KB, RMAX, NT>(a, src, le.begin, len, raw, sx); break;
+    }
   }
 }
 
@@ -167,7 +186,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 && KB <= 8 ? 4 : NT <= 512 ? 2 :
 template <int KB> __global__ void __launch_bounds__(MID_NT, KB == 16 ? 4 : 8) k_leaf_mid(SortArgs a) {
   using C = typename KT<KB>::Code;
   constexpr unsigned MAXK = mid_max_keys(KB);
-  __shared__ C sx[MAXK + MAXK / 32];
+  __shared__ C sx[MAXK + MAXK / 8];
   __shared__ unsigned long long s_idx;
   const unsigned long long n = a.hdr->n_leaf_mid;
   if (a.hdr->abort) return;
@@ -185,8 +204,7 @@ template <int KB> __global__ void __launch_bounds__(MID_NT, KB == 16 ? 4 : 8) k_
     const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
     const bool raw = le.flags & SEG_RAW;
     const unsigned len = le.len;
-    if (len <= 4 * MID_NT) block_leaf<KB, 4, MID_NT>(a, src, le.begin, len, raw, sx);
-    else if (len <= 8 * MID_NT || KB == 16) block_leaf<KB, 8, MID_NT>(a, src, le.begin, len, raw, sx);
+    if (len <= 8 * MID_NT || KB == 16) block_leaf<KB, 8, MID_NT>(a, src, le.begin, len, raw, sx);
     else block_leaf<KB, (KB == 16 ? 8 : 16), MID_NT>(a, src, le.begin, len, raw, sx);
   }
 }
@@ -211,7 +229,7 @@ template <int KB, int NT> int leaf_block_grid(size_t smem) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_leaf_block<KB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)leaf_block_smem(KB, max_leaf_cutoff(KB)));
+                         (int)leaf_block_smem(KB, max_leaf_cutoff(KB), NT));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_leaf_block<KB, NT>, NT, smem);
     grid = sms * (per > 0 ? per : 1);
     last = smem;
@@ -233,12 +251,18 @@ template <int KB> int leaf_warp_grid() {
 
 template <int KB> cudaError_t leaf_block_impl(const SortArgs &a, cudaStream_t s) {
   const unsigned C = a.leaf_cutoff < 1024 ? 1024 : a.leaf_cutoff;
-  const size_t smem = leaf_block_smem(KB, C);
   if constexpr (KB == 16) {   // cutoff <= 4096: at most 8 keys per thread at 512 threads
-    if (a.leaf_threads == 256) k_leaf_block<KB, 256><<<leaf_block_grid<KB, 256>(smem), 256, smem, s>>>(a);
-    else k_leaf_block<KB, 512><<<leaf_block_grid<KB, 512>(smem), 512, smem, s>>>(a);
+    if (a.leaf_threads == 256) {
+      const size_t smem = leaf_block_smem(KB, C, 256);
+      k_leaf_block<KB, 256><<<leaf_block_grid<KB, 256>(smem), 256, smem, s>>>(a);
+    } else {
+      const size_t smem = leaf_block_smem(KB, C, 512);
+      k_leaf_block<KB, 512><<<leaf_block_grid<KB, 512>(smem), 512, smem, s>>>(a);
+    }
   } else {
-    switch (leaf_nt_for(C, a.leaf_threads)) {
+    const int nt = leaf_nt_for(C, a.leaf_threads);
+    const size_t smem = leaf_block_smem(KB, C, nt);
+    switch (nt) {
       case 1024: k_leaf_block<KB, 1024><<<leaf_block_grid<KB, 1024>(smem), 1024, smem, s>>>(a); break;
       case 512: k_leaf_block<KB, 512><<<leaf_block_grid<KB, 512>(smem), 512, smem, s>>>(a); break;
       default: k_leaf_block<KB, 256><<<leaf_block_grid<KB, 256>(smem), 256, smem, s>>>(a); break;

@@ -199,14 +199,17 @@ __device__ unsigned long long reserve(const SortArgs &a, unsigned long long *cou
 // The leaf list for a range of m keys (at most the cutoff): warp leaves up to
 // WARP_LEAF_MAX keys, mid-size leaves up to a.mid_max, block leaves above.
 struct LeafList {
-  unsigned long long *n, *stat;
+  unsigned long long *n, *stat, *keys;
   LeafEntry *list;
   unsigned cap;
 };
 __device__ __forceinline__ LeafList leaf_list(const SortArgs &a, uint64_t m) {
-  if (m <= WARP_LEAF_MAX) return LeafList{&a.hdr->n_leaf_warp, &a.hdr->leaves_warp, a.leaf_warp, a.cap_leaf_warp};
-  if (m <= a.mid_max) return LeafList{&a.hdr->n_leaf_mid, &a.hdr->leaves_mid, a.leaf_mid, a.cap_leaf_mid};
-  return LeafList{&a.hdr->n_leaf_block, &a.hdr->leaves_block, a.leaf_block, a.cap_leaf_block};
+  if (m <= WARP_LEAF_MAX)
+    return LeafList{&a.hdr->n_leaf_warp, &a.hdr->leaves_warp, &a.hdr->leaf_keys_warp, a.leaf_warp, a.cap_leaf_warp};
+  if (m <= a.mid_max)
+    return LeafList{&a.hdr->n_leaf_mid, &a.hdr->leaves_mid, &a.hdr->leaf_keys_mid, a.leaf_mid, a.cap_leaf_mid};
+  return LeafList{&a.hdr->n_leaf_block, &a.hdr->leaves_block, &a.hdr->leaf_keys_block, a.leaf_block,
+                  a.cap_leaf_block};
 }
 
 // A finished range of keys that only needs sorting by a leaf network
@@ -220,6 +223,7 @@ __device__ void emit_leaf(const SortArgs &a, uint64_t b, uint64_t m, unsigned fl
     L.list[i] = LeafEntry{b, (unsigned)m, flags};
     atomicAdd(L.stat, 1ull);
     atomicAdd(&a.hdr->leaf_keys, m);
+    atomicAdd(L.keys, m);
   }
 }
 
@@ -690,6 +694,7 @@ __device__ void finish_kway_scatter(const SortArgs &a, const SegDesc &sd, unsign
           L.list[i] = LeafEntry{cb, (unsigned)mc, parity};
           atomicAdd(L.stat, 1ull);
           atomicAdd(&a.hdr->leaf_keys, mc);
+          atomicAdd(L.keys, mc);
         } else {
           raise_error(a, ERR_INTERNAL);
         }

@@ -99,4 +99,128 @@ template <class C, int R> __device__ __forceinline__ void warp_sort(C (&k)[R], u
   group_sort<C, R, 32>(k, lane, nullptr);
 }
 
+// ---------------------------------------------------------------------------
+// Block sorts for leaves of more than a few hundred keys: the register
+// networks above build sorted runs of L0 keys inside each warp, then
+// merge-path merges in shared memory join runs pairwise (L0 -> 2 L0 -> ...).
+// A bitonic merge of two runs of L keys costs log2(2L) compare-exchange
+// steps per key; a merge-path merge costs one comparison per key plus a
+// binary search per thread, so past a few dozen keys per run merging is the
+// cheaper way to finish the base case. Runs need not be powers of two: only
+// the slots up to the leaf length rounded up to L0 take part.
+// ---------------------------------------------------------------------------
+
+// Shared-memory slot of logical index i: one spare slot per R keys, so that
+// the R keys of consecutive threads (stride R + 1) fall in distinct banks.
+template <int R> __device__ __forceinline__ unsigned spad(unsigned i) { return i + i / (unsigned)R; }
+
+// A code above or equal to every code of the key type: read past the end of
+// a run, so the other run's keys are taken first.
+template <class C> __device__ __forceinline__ C ones_code();
+template <> __device__ __forceinline__ uint32_t ones_code<uint32_t>() { return ~0u; }
+template <> __device__ __forceinline__ uint64_t ones_code<uint64_t>() { return ~0ull; }
+template <> __device__ __forceinline__ U128 ones_code<U128>() { return U128{~0ull, ~0ull}; }
+
+// Bitonic phases joining runs of L keys up to runs of LEND keys; a run of
+// LEND keys spans LEND/R <= 32 lanes, so every step is a register pairing
+// or a shuffle.
+template <class C, int R, unsigned L, unsigned LEND>
+__device__ __forceinline__ void warp_phases(C (&k)[R], unsigned lane) {
+  if constexpr (L < LEND) {
+    constexpr unsigned steps = ilog2(L) + 1;
+#pragma unroll
+    for (unsigned s = 0; s < steps; ++s) merge_step<C, R, 32>(k, vq_merge_step(L, R, s), lane, nullptr);
+    warp_phases<C, R, 2 * L, LEND>(k, lane);
+  }
+}
+
+// One merge-path round: the ns slots form sorted runs of L keys; afterwards
+// they form sorted runs of 2L. Thread t holds logical slots t*R .. t*R+R-1
+// before and after. A pair whose second run is empty is already merged.
+// Rounds of runs within one warp synchronise the warp only.
+template <class C, int R, int NT, unsigned L>
+__device__ __forceinline__ void mp_round(C (&k)[R], unsigned t, unsigned ns, C *sx) {
+  constexpr bool WARP = 2 * L <= 32u * R;
+  const unsigned o = t * R;
+  const bool act = o < ns;
+  if (act) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) sx[spad<R>(o + r)] = k[r];
+  }
+  if constexpr (WARP) __syncwarp(); else __syncthreads();
+  const unsigned base = o & ~(2 * L - 1);
+  if (act && ns - base > L) {
+    // runs A = [base, base + L) (full) and B = [base + L, base + L + lb)
+    const unsigned d = o - base, lb = min(L, ns - base - L);
+    const C *A = sx + spad<R>(base), *B = sx + spad<R>(base + L);
+    // merge path: how many of the first d outputs come from A (ties: A first)
+    unsigned lo = d > lb ? d - lb : 0, hi = min(d, L);
+    while (lo < hi) {
+      const unsigned mid = (lo + hi) >> 1;
+      if (lt(B[spad<R>(d - 1 - mid)], A[spad<R>(mid)])) hi = mid;
+      else lo = mid + 1;
+    }
+    // serial merge of the thread's R outputs: one shared-memory read each
+    unsigned ia = lo, ib = d - lo;
+    C x = ia < L ? A[spad<R>(ia)] : ones_code<C>();
+    C y = ib < lb ? B[spad<R>(ib)] : ones_code<C>();
+    const unsigned la = L, da = spad<R>(base), db = spad<R>(base + L);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const bool tb = lt(y, x);
+      k[r] = tb ? y : x;
+      if (r + 1 < R) {
+        ia += tb ? 0u : 1u;
+        ib += tb ? 1u : 0u;
+        const unsigned i = tb ? ib : ia, lim = tb ? lb : la, d0 = tb ? db : da;
+        const C v = i < lim ? sx[d0 + spad<R>(i)] : ones_code<C>();
+        x = tb ? x : v;
+        y = tb ? v : y;
+      }
+    }
+  }
+  if constexpr (WARP) __syncwarp(); else __syncthreads();
+}
+
+// Rounds for run lengths L, 2L, ... while runs are shorter than ns (the
+// test is uniform over the block, so every thread takes the same barriers).
+template <class C, int R, int NT, unsigned L>
+__device__ __forceinline__ void mp_rounds(C (&k)[R], unsigned t, unsigned ns, C *sx) {
+  if constexpr (L < (unsigned)(NT * R)) {
+    if (L < ns) {
+      mp_round<C, R, NT, L>(k, t, ns, sx);
+      mp_rounds<C, R, NT, 2 * L>(k, t, ns, sx);
+    }
+  }
+}
+
+// Sorts the ns = (leaf length rounded up to L0) slots held by the first
+// ns/R of NT threads (the others hold nothing and only take the barriers).
+// Afterwards thread t holds logical slots t*R .. t*R+R-1. sx: spad<R>(NT*R)
+// codes of shared memory.
+template <class C, int R, int NT, unsigned L0>
+__device__ __forceinline__ void merge_sort_block(C (&k)[R], unsigned t, unsigned ns, C *sx) {
+  static_assert(L0 >= (unsigned)R && L0 <= 32u * R, "runs of the register stage fit one warp");
+  if ((t & ~31u) * R < ns) {   // warps holding slots
+    if constexpr (R > 1) column_sort<C, R>(k);
+    warp_phases<C, R, (unsigned)R, L0>(k, t & 31u);
+  }
+  mp_rounds<C, R, NT, L0>(k, t, ns, sx);
+}
+
+// Comparisons made by merge_sort_block on ns slots (statistics): the
+// column networks, the bitonic phases and, per merge round, one per output
+// key plus the binary searches.
+template <int R, int NT, unsigned L0> __device__ __forceinline__ unsigned long long merge_sort_cmps(unsigned ns) {
+  constexpr unsigned col = R == 2 ? 1 : R == 4 ? 5 : R == 8 ? 19 : R == 16 ? 60 : 0;
+  unsigned long long c = (unsigned long long)(ns / R) * col;
+  for (unsigned L = R; L < L0; L *= 2) c += (unsigned long long)(ns / 2) * (ilog2(L) + 1);
+  for (unsigned L = L0; L < ns; L *= 2) {
+    const unsigned full = ns / (2 * L) * (2 * L), rest = ns - full;   // keys in pairs with a second run
+    const unsigned merged = full + (rest > L ? rest : 0);
+    c += merged + (unsigned long long)(merged / R) * (ilog2(L) + 1);
+  }
+  return c;
+}
+
 }  // namespace vq
