@@ -55,32 +55,6 @@ def test_one_million(vq, oracle_mod, dtype):
     check_sort(vq, oracle_mod, dtype, a, True)
 
 
-def test_full_size_u64_uniform(vq, oracle_mod):
-    """1e8 uniform u64 keys (the benchmark's workload) against the oracle."""
-    a = inputs.make("u64", 100_000_000, "uniform")
-    check_sort(vq, oracle_mod, "u64", a, True)
-    st = vq.stats()
-    assert st["fallback_ranges"] == 0
-    assert st["max_depth"] <= 2 * 26 + 4
-
-
-@pytest.mark.parametrize("dtype,dist,asc", [("f32", "uniform", False), ("i32", "organpipe", True),
-                                            ("i16", "distinct16", True), ("u64", "reverse", False)])
-def test_full_size_properties(vq, oracle_mod, dtype, dist, asc):
-    """1e8 keys: the output's codes (oracle codec) never decrease and the
-    output is a permutation of the input (equal sorted bit patterns)."""
-    n = 100_000_000
-    a = inputs.make(dtype, n, dist, specials=True)
-    t = to_dev(a, dtype)
-    vq.sort_(t, dtype, descending=not asc)
-    got = to_host(t, dtype, a)
-    assert vq.last_device_status() == 0
-    codes = oracle_mod.encode(got, dtype, asc)
-    assert bool((codes[1:] >= codes[:-1]).all())
-    ut = {2: np.uint16, 4: np.uint32, 8: np.uint64}[a.itemsize]
-    assert np.array_equal(np.sort(got.view(ut)), np.sort(a.view(ut)))
-
-
 @pytest.mark.parametrize("dtype", ("u128", "kv64"))
 def test_wide_keys_c3(vq, oracle_mod, dtype):
     """2.5e7 u128 keys / kv64 pairs with 10 % duplicated keys (pairing kept)."""
