@@ -11,7 +11,8 @@
 //
 // The array holds up to NOALLOC_TILES partition tiles, so one call accepts
 // at most NOALLOC_TILES * ((32768 - 16) / key_bytes) keys. Every GPU that
-// loads the library keeps the array (about 513 KiB) until the process exits.
+// loads the library keeps the array (528,896 bytes, about 517 KiB) until the
+// process exits.
 #include <cstring>
 #include <mutex>
 
@@ -27,6 +28,7 @@ constexpr size_t NOALLOC_HDR = 512;                          // Header, rounded 
 constexpr size_t NOALLOC_SEGS = 64 * sizeof(SegDesc);        // the one range (room to spare)
 constexpr size_t NOALLOC_BYTES = NOALLOC_HDR + NOALLOC_SEGS + (size_t)NOALLOC_TILES * 8;
 static_assert(sizeof(Header) <= NOALLOC_HDR, "header does not fit");
+static_assert(NOALLOC_BYTES == 528896, "the size stated above and in the header");
 
 // The scratch shared by every call in the process. Host code must not use
 // this name as an address: it is a host-side stand-in. The device address
