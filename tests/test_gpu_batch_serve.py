@@ -37,13 +37,15 @@ def test_autotune_picks_valid_settings(vq, oracle_mod):
     n = int(off[-1])
     a = inputs.make("u32", n, "uniform", seed=4)
     cands = batch.candidates("u32")[:6]
+    before = batch.current_settings()
     res = batch.autotune(to_dev(a, "u32"), off, "u32", reps=1, candidate_list=cands, force=True)
+    assert batch.current_settings() == before     # autotune puts the settings back
     assert res["settings"] in cands + [batch.DEFAULT]
     assert res["ms"] > 0 and res["tried"] == len(cands) + 1
     b = batch.SegmentedBatch(to_dev(a, "u32"), off, "u32", settings=res["settings"])
     b.sort()
     assert same_bits(to_host(b.keys, "u32", a), oracle_mod.sort_segmented(a, off, "u32", True))
-    assert batch.current_settings() == batch.DEFAULT or True
+    assert batch.current_settings() == before     # and so does a sort under tuned settings
 
 
 def test_served_results_equal_solo_results(vq, oracle_mod):

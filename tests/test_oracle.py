@@ -6,6 +6,7 @@ the IEEE totalOrder definition (tests/total_order.py), closed forms, or
 invariants that hold at any size.
 """
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -187,13 +188,28 @@ def test_all_equal_and_two_values_terminate(oracle_mod):
     np.testing.assert_array_equal(oracle_mod.sort(c, "u32", True), np.sort(c))
 
 
+def _median3_network():
+    """The modules of the paper's median-of-3 network (Sec. 2.2), read from
+    tests/golden/median3_network.txt."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "median3_network.txt")
+    with open(path) as f:
+        nums = [int(x) for ln in f if not ln.startswith("#") for x in ln.split()]
+    return list(zip(nums[0::2], nums[1::2]))
+
+
 def test_median3_network_exhaustive(oracle_mod):
-    """(0,2)(0,1)(1,2) yields the median of every 3-tuple, duplicates included."""
-    for t in itertools.product(range(3), repeat=3):
-        assert oracle_mod.median3(*t) == sorted(t)[1]
-    big = [0, 2**63, 2**64 - 1]
-    for t in itertools.permutations(big):
-        assert oracle_mod.median3(*t) == 2**63
+    """The paper's network, applied as compare-exchange modules, leaves the
+    median of every 3-tuple (duplicates included) in slot 1, and the
+    oracle's median3 returns that slot."""
+    net = _median3_network()
+    assert net == [(0, 2), (0, 1), (1, 2)]
+    for t in list(itertools.product(range(3), repeat=3)) + list(itertools.permutations([0, 2**63, 2**64 - 1])):
+        v = list(t)
+        for i, j in net:
+            if v[j] < v[i]:
+                v[i], v[j] = v[j], v[i]
+        assert v[1] == sorted(t)[1]
+        assert oracle_mod.median3(*t) == v[1]
 
 
 def _numpy_sfc64_stream(seed, count):
