@@ -111,12 +111,13 @@ __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, u
   const unsigned ns = (len + L0 - 1) / L0 * L0;
   const unsigned nta = ns / R;
   C k[R];
+  const void *sb = (const unsigned char *)src + b * KB;
   if (t < nta) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const unsigned j = r * nta + t;
       if (j < len) {
-        C c = load_key<KB>(src, b + j);
+        C c = load_key<KB>(sb, j);
         k[r] = raw ? encode<KB>(c, a.codec) : c;
       } else {
         k[r] = KT<KB>::max_code();
@@ -133,10 +134,27 @@ __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, u
   }
   __syncthreads();
   const C *__restrict__ st = sx;
+  void *ob = (unsigned char *)a.out + b * KB;
 #pragma unroll 4
-  for (unsigned j = t; j < len; j += NT) store_key<KB>(a.out, b + j, decode<KB>(st[spad<R>(j)], a.codec));
+  for (unsigned j = t; j < len; j += NT) store_key<KB>(ob, j, decode<KB>(st[spad<R>(j)], a.codec));
   if (t == 0) atomicAdd(&a.hdr->leaf_ce, merge_sort_cmps<R, NT, L0>(ns));
   __syncthreads();
+}
+
+// Starts pulling the keys of leaf `idx` (if it exists) from HBM into L2 with
+// one bulk prefetch, so that its loads, issued after the current leaf is
+// sorted, hit L2. The 16-byte aligned span around the keys stays within the
+// memory pages of the array.
+template <int KB>
+__device__ __forceinline__ void prefetch_leaf_l2(const SortArgs &a, const LeafEntry *list, unsigned long long idx,
+                                                 unsigned long long n) {
+  if (idx >= n) return;
+  const LeafEntry le = list[idx];
+  if (le.len == 0 || le.begin + le.len > a.n_total) return;
+  const uintptr_t src = (uintptr_t)((le.flags & SEG_PARITY) ? a.alt : a.keys);
+  const uintptr_t g0 = (src + le.begin * KB) & ~(uintptr_t)15;
+  const uintptr_t g1 = (src + (le.begin + le.len) * KB + 15) & ~(uintptr_t)15;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g0), "r"((unsigned)(g1 - g0)) : "memory");
 }
 
 // NT threads sort one range of up to RMAX*NT keys at a time.
@@ -145,39 +163,45 @@ __global__ void __launch_bounds__(NT, NT <= 256 && KB <= 8 ? 4 : NT <= 512 ? 2 :
   constexpr int RMAX = leaf_rmax(KB, NT);
   using C = typename KT<KB>::Code;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long s_idx;
+  __shared__ unsigned long long s_idx, s_next;
   C *sx = (C *)smem;
   const unsigned long long n = a.hdr->n_leaf_block;
   if (a.hdr->abort) return;
-  for (;;) {
-    if (threadIdx.x == 0) s_idx = atomicAdd(&a.hdr->cur_leaf_block, 1ull);
-    __syncthreads();
-    const unsigned long long idx = s_idx;
-    __syncthreads();
-    if (idx >= n) break;
+  if (threadIdx.x == 0) s_idx = atomicAdd(&a.hdr->cur_leaf_block, 1ull);
+  __syncthreads();
+  unsigned long long idx = s_idx;
+  while (idx < n) {
+    if (threadIdx.x == 0) {
+      const unsigned long long nx = atomicAdd(&a.hdr->cur_leaf_block, 1ull);
+      s_next = nx;
+      prefetch_leaf_l2<KB>(a, a.leaf_block, nx, n);
+    }
     const LeafEntry le = a.leaf_block[idx];
     // guard: inside the array, and no longer than the cutoff the shared
     // memory was sized for
     if (le.begin + le.len > a.n_total || le.len > (unsigned)(RMAX * NT) ||
         le.len > (a.leaf_cutoff < 1024 ? 1024u : a.leaf_cutoff)) {
       if (threadIdx.x == 0) guard_failed(a, GUARD_LEAF);
-      continue;
-    }
-    const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
-    const bool raw = le.flags & SEG_RAW;
-    const unsigned len = le.len;
-    if (le.flags & LEAF_COPY) {
-      for (unsigned j = threadIdx.x; j < len; j += NT) {
-        const C c = load_key<KB>(src, le.begin + j);
-        store_key<KB>(a.out, le.begin + j, decode<KB>(raw ? encode<KB>(c, a.codec) : c, a.codec));
+    } else {
+      const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
+      const bool raw = le.flags & SEG_RAW;
+      const unsigned len = le.len;
+      if (le.flags & LEAF_COPY) {
+        for (unsigned j = threadIdx.x; j < len; j += NT) {
+          const C c = load_key<KB>(src, le.begin + j);
+          store_key<KB>(a.out, le.begin + j, decode<KB>(raw ? encode<KB>(c, a.codec) : c, a.codec));
+        }
+      } else {
+        switch (leaf_r_for(len, NT, RMAX)) {
+          case 4: block_leaf<KB, 4, NT>(a, src, le.begin, len, raw, sx); break;
+          case 8: block_leaf<KB, (RMAX < 8 ? RMAX : 8), NT>(a, src, le.begin, len, raw, sx); break;
+          default: block_leaf<KB, RMAX, NT>(a, src, le.begin, len, raw, sx); break;
+        }
       }
-      continue;
     }
-    switch (leaf_r_for(len, NT, RMAX)) {
-      case 4: block_leaf<KB, 4, NT>(a, src, le.begin, len, raw, sx); break;
-      case 8: block_leaf<KB, (RMAX < 8 ? RMAX : 8), NT>(a, src, le.begin, len, raw, sx); break;
-      default: block_leaf<KB, RMAX, NT>(a, src, le.begin, len, raw, sx); break;
-    }
+    __syncthreads();
+    idx = s_next;
+    __syncthreads();
   }
 }
 
@@ -187,25 +211,31 @@ template <int KB> __global__ void __launch_bounds__(MID_NT, KB == 16 ? 4 : 8) k_
   using C = typename KT<KB>::Code;
   constexpr unsigned MAXK = mid_max_keys(KB);
   __shared__ C sx[MAXK + MAXK / 8];
-  __shared__ unsigned long long s_idx;
+  __shared__ unsigned long long s_idx, s_next;
   const unsigned long long n = a.hdr->n_leaf_mid;
   if (a.hdr->abort) return;
-  for (;;) {
-    if (threadIdx.x == 0) s_idx = atomicAdd(&a.hdr->cur_leaf_mid, 1ull);
-    __syncthreads();
-    const unsigned long long idx = s_idx;
-    __syncthreads();
-    if (idx >= n) break;
+  if (threadIdx.x == 0) s_idx = atomicAdd(&a.hdr->cur_leaf_mid, 1ull);
+  __syncthreads();
+  unsigned long long idx = s_idx;
+  while (idx < n) {
+    if (threadIdx.x == 0) {
+      const unsigned long long nx = atomicAdd(&a.hdr->cur_leaf_mid, 1ull);
+      s_next = nx;
+      prefetch_leaf_l2<KB>(a, a.leaf_mid, nx, n);
+    }
     const LeafEntry le = a.leaf_mid[idx];
     if (le.begin + le.len > a.n_total || le.len > MAXK) {   // guard
       if (threadIdx.x == 0) guard_failed(a, GUARD_LEAF);
-      continue;
+    } else {
+      const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
+      const bool raw = le.flags & SEG_RAW;
+      const unsigned len = le.len;
+      if (len <= 8 * MID_NT || KB == 16) block_leaf<KB, 8, MID_NT>(a, src, le.begin, len, raw, sx);
+      else block_leaf<KB, (KB == 16 ? 8 : 16), MID_NT>(a, src, le.begin, len, raw, sx);
     }
-    const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
-    const bool raw = le.flags & SEG_RAW;
-    const unsigned len = le.len;
-    if (len <= 8 * MID_NT || KB == 16) block_leaf<KB, 8, MID_NT>(a, src, le.begin, len, raw, sx);
-    else block_leaf<KB, (KB == 16 ? 8 : 16), MID_NT>(a, src, le.begin, len, raw, sx);
+    __syncthreads();
+    idx = s_next;
+    __syncthreads();
   }
 }
 

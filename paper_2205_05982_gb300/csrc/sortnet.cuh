@@ -134,14 +134,32 @@ __device__ __forceinline__ void warp_phases(C (&k)[R], unsigned lane) {
   }
 }
 
+// A code below or equal to every code: read before the start of a run.
+template <class C> __device__ __forceinline__ C zero_code();
+template <> __device__ __forceinline__ uint32_t zero_code<uint32_t>() { return 0u; }
+template <> __device__ __forceinline__ uint64_t zero_code<uint64_t>() { return 0ull; }
+template <> __device__ __forceinline__ U128 zero_code<U128>() { return U128{0ull, 0ull}; }
+
 // One merge-path round: the ns slots form sorted runs of L keys; afterwards
 // they form sorted runs of 2L. Thread t holds logical slots t*R .. t*R+R-1
 // before and after. A pair whose second run is empty is already merged.
-// Rounds of runs within one warp synchronise the warp only.
-template <class C, int R, int NT, unsigned L>
-__device__ __forceinline__ void mp_round(C (&k)[R], unsigned t, unsigned ns, C *sx) {
-  constexpr bool WARP = 2 * L <= 32u * R;
-  const unsigned o = t * R;
+//
+// Each thread finds where its first output splits the two runs (binary
+// search, ties: the first run's key first) and takes the split of its last
+// output + 1 from the next thread (a shuffle, or shared memory across
+// warps). It then fills its R outputs with two independent chains, one
+// taking the smaller head from the front, one the larger tail from the
+// back, R/2 steps each: the front chain yields the R/2 smallest keys after
+// the first split, the back chain the R/2 largest before the last one, and
+// the two chains overlap their shared-memory latencies. Reads past a run's
+// end (front) or before its start (back) give a code no key passes; where a
+// key equals it, the bits are the same either way. Rounds of runs within one
+// warp synchronise the warp only.
+template <class C, int R, int NT, bool WARP>
+__device__ __forceinline__ void mp_round(C (&k)[R], unsigned t, unsigned ns, C *sx, const unsigned L) {
+  constexpr int H = R / 2;
+  static_assert(R >= 2 && R % 2 == 0, "two chains of R/2 outputs");
+  const unsigned o = t * R, lane = t & 31u;
   const bool act = o < ns;
   if (act) {
 #pragma unroll
@@ -149,49 +167,78 @@ __device__ __forceinline__ void mp_round(C (&k)[R], unsigned t, unsigned ns, C *
   }
   if constexpr (WARP) __syncwarp(); else __syncthreads();
   const unsigned base = o & ~(2 * L - 1);
-  if (act && ns - base > L) {
-    // runs A = [base, base + L) (full) and B = [base + L, base + L + lb)
-    const unsigned d = o - base, lb = min(L, ns - base - L);
-    const C *A = sx + spad<R>(base), *B = sx + spad<R>(base + L);
-    // merge path: how many of the first d outputs come from A (ties: A first)
-    unsigned lo = d > lb ? d - lb : 0, hi = min(d, L);
+  const bool merge = act && ns - base > L;
+  // runs A = [base, base + L) (full) and B = [base + L, base + L + lb)
+  const unsigned d = o - base, lb = merge ? min(L, ns - base - L) : 0u;
+  const unsigned da = spad<R>(base), db = spad<R>(base + L);
+  const C *A = sx + da, *B = sx + db;
+  unsigned lo = 0;
+  if (merge) {
+    // merge path: how many of the first d outputs come from A
+    lo = d > lb ? d - lb : 0;
+    unsigned hi = min(d, L);
     while (lo < hi) {
       const unsigned mid = (lo + hi) >> 1;
       if (lt(B[spad<R>(d - 1 - mid)], A[spad<R>(mid)])) hi = mid;
       else lo = mid + 1;
     }
-    // serial merge of the thread's R outputs: one shared-memory read each
+  }
+  // the next thread's split is where this thread's outputs end
+  unsigned lo_next = __shfl_down_sync(0xFFFFFFFFu, lo, 1);
+  if constexpr (!WARP) {
+    __shared__ unsigned s_first[NT / 32];
+    if (lane == 0) s_first[t >> 5] = lo;
+    __syncthreads();
+    if (lane == 31 && t + 1 < (unsigned)NT) lo_next = s_first[(t >> 5) + 1];
+  }
+  if (merge) {
+    const unsigned ja = d + R == L + lb ? L : lo_next;   // the pair's last thread ends at (L, lb)
+    // ea, eb: keys of A and B not yet taken by the back chain; signed, as a
+    // tie with the sentinel below a run takes the sentinel and steps past 0
     unsigned ia = lo, ib = d - lo;
+    int ea = (int)ja, eb = (int)(d + R - ja);
     C x = ia < L ? A[spad<R>(ia)] : ones_code<C>();
     C y = ib < lb ? B[spad<R>(ib)] : ones_code<C>();
-    const unsigned la = L, da = spad<R>(base), db = spad<R>(base + L);
+    C u = ea > 0 ? A[spad<R>((unsigned)ea - 1)] : zero_code<C>();
+    C w = eb > 0 ? B[spad<R>((unsigned)eb - 1)] : zero_code<C>();
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const bool tb = lt(y, x);
+    for (int r = 0; r < H; ++r) {
+      const bool tb = lt(y, x);   // front: B's head strictly smaller
+      const bool ta = lt(w, u);   // back: A's tail strictly larger
       k[r] = tb ? y : x;
-      if (r + 1 < R) {
+      k[R - 1 - r] = ta ? u : w;
+      if (r + 1 < H) {
         ia += tb ? 0u : 1u;
         ib += tb ? 1u : 0u;
-        const unsigned i = tb ? ib : ia, lim = tb ? lb : la, d0 = tb ? db : da;
+        ea -= ta ? 1 : 0;
+        eb -= ta ? 0 : 1;
+        const unsigned i = tb ? ib : ia, lim = tb ? lb : L, d0 = tb ? db : da;
+        const int e = ta ? ea : eb;
+        const unsigned d1 = ta ? da : db;
         const C v = i < lim ? sx[d0 + spad<R>(i)] : ones_code<C>();
+        const C v2 = e > 0 ? sx[d1 + spad<R>((unsigned)e - 1)] : zero_code<C>();
         x = tb ? x : v;
         y = tb ? v : y;
+        u = ta ? v2 : u;
+        w = ta ? w : v2;
       }
     }
   }
   if constexpr (WARP) __syncwarp(); else __syncthreads();
 }
 
-// Rounds for run lengths L, 2L, ... while runs are shorter than ns (the
-// test is uniform over the block, so every thread takes the same barriers).
-template <class C, int R, int NT, unsigned L>
+// Rounds for run lengths L0, 2 L0, ... while runs are shorter than ns (the
+// test is uniform over the block, so every thread takes the same barriers):
+// first the rounds whose run pairs fit one warp, then the block-wide ones.
+// The rounds are loops, not unrolled: one body of each kind keeps the code
+// small enough for the instruction cache.
+template <class C, int R, int NT, unsigned L0>
 __device__ __forceinline__ void mp_rounds(C (&k)[R], unsigned t, unsigned ns, C *sx) {
-  if constexpr (L < (unsigned)(NT * R)) {
-    if (L < ns) {
-      mp_round<C, R, NT, L>(k, t, ns, sx);
-      mp_rounds<C, R, NT, 2 * L>(k, t, ns, sx);
-    }
-  }
+  unsigned L = L0;
+#pragma unroll 1
+  for (; L < ns && 2 * L <= 32u * R; L *= 2) mp_round<C, R, NT, true>(k, t, ns, sx, L);
+#pragma unroll 1
+  for (; L < ns; L *= 2) mp_round<C, R, NT, false>(k, t, ns, sx, L);
 }
 
 // Sorts the ns = (leaf length rounded up to L0) slots held by the first
