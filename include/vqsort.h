@@ -78,6 +78,22 @@ vq_status vqsort_sort(vq_dtype dt, void *d_keys, size_t n, int ascending, void *
    vqsort_sort(VQ_KV64, ...). */
 vq_status vqsort_sort_kv(void *d_pairs, size_t n, int ascending, void *stream);
 
+/* Key-only order of the same pairs (Sec. 2.4, 64-bit keys with 64-bit
+   data; Sec. 5, Quicksort is not stable): d_pairs holds n structs
+   {uint64_t key; uint64_t value;}; afterwards the keys are non-decreasing
+   (ascending = 0: non-increasing) and the pairs are the input's pairs, each
+   value still beside its key. Only the 64-bit key is compared, so pairs
+   with equal keys come out in an unspecified order (it may differ from
+   vqsort_sort_kv's). A leaf range holding the key 0 or 2^64 - 1 is finished
+   in the (key, value) order, one of the valid orders. In place on
+   `stream`, library-owned workspace per (device, stream); the _ws form
+   takes a caller-owned workspace of vqsort_workspace_bytes(VQ_KV64, n, 1)
+   bytes (256-byte aligned) and allocates nothing. Argument checks and
+   status as vqsort_sort. */
+vq_status vqsort_sort_kv_by_key(void *d_pairs, size_t n, int ascending, void *stream);
+vq_status vqsort_sort_kv_by_key_ws(void *d_pairs, size_t n, int ascending, void *d_ws, size_t ws_bytes,
+                                   void *stream);
+
 /* Stable sort (Sec. 5: appending a unique row identifier below the key makes
    Quicksort stable). Sorts the n keys at d_keys in place, in the same order
    as vqsort_sort, and writes to d_rows (device, n uint64_t, 8-byte aligned)
@@ -119,10 +135,10 @@ vq_status vqsort_sort_segmented_ws(vq_dtype dt, void *d_keys, size_t n_total,
 
 /* End-to-end sort of a HOST array: copies h_keys to the device, sorts, and
    waits. Uses a library-owned stream and device buffer on the current
-   device. If h_keys is pinned (page-locked and mapped), the leaf kernels
-   write the sorted keys straight into it, so the download overlaps the
-   leaves' work (VQ_OPT_HOST_DIRECT = 0: copied back after the sort);
-   pageable memory is copied back after the sort. */
+   device. The sorted keys are copied back by a copy engine after the sort;
+   with VQ_OPT_HOST_DIRECT = 1 the leaf kernels write them straight into a
+   pinned (page-locked, mapped) array instead. Pageable memory is always
+   copied back. */
 vq_status vqsort_sort_host(vq_dtype dt, void *h_keys, size_t n, int ascending);
 
 /* The same end-to-end sort of a HOST array, enqueued on `stream` without
@@ -190,6 +206,15 @@ vq_status vqsort_partition_noalloc(vq_dtype dt, const void *d_in, void *d_out, s
    sort has used that one). */
 vq_status vqsort_last_device_status(const void *d_ws, void *stream);
 
+/* Enqueues on `stream` a copy of the device-side status word of the
+   caller-owned workspace d_ws into *h_status (8 bytes of host memory; page-
+   locked memory keeps the call asynchronous). Once the stream has passed
+   this point, *h_status holds the vq_status latched by the sorts enqueued
+   before it on that workspace (VQ_OK = 0). For serving loops that must not
+   wait for a stream to learn whether a sort succeeded. VQ_ERR_INVALID for
+   null pointers. */
+vq_status vqsort_device_status_async(const void *d_ws, uint64_t *h_status, void *stream);
+
 /* Counters of the last sort on a workspace (waits for `stream`). */
 typedef struct vq_stats {
   uint64_t keys_partitioned;     /* sum over partition levels (two-way and K-way) of keys
@@ -213,8 +238,13 @@ typedef struct vq_stats {
   uint64_t partition_blocks;     /* thread blocks of the persistent partition kernel */
   uint64_t leaves_mid;           /* ranges of 513..2048 keys (16-byte keys: ..1024) sorted by
                                     128-thread blocks */
-  uint64_t leaf_ce;              /* compare-exchanges run by the leaf sorting networks
-                                    (padded sizes included) */
+  uint64_t leaf_ce;              /* key comparisons of the leaf sorts: compare-exchanges of
+                                    the register networks plus the comparisons of the
+                                    shared-memory merges (padding slots included) */
+  uint64_t leaf_keys_warp;       /* keys of the ranges sorted by one warp */
+  uint64_t leaf_keys_mid;        /* keys of the ranges sorted by 128-thread blocks */
+  uint64_t leaf_keys_block;      /* keys of the ranges sorted by the block leaves (all-equal
+                                    ranges, copied by the same kernel, are in equal_keys) */
 } vq_stats;
 vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out);
 
@@ -246,10 +276,13 @@ typedef enum vq_option {
                                with equality buckets when the splitters repeat; 0: every
                                level is the paper's two-way Partition. The output is the
                                same. */
-  VQ_OPT_HOST_DIRECT = 8    /* host-array sorts of pinned memory: 1 (default): the leaf
-                               kernels store the result straight into the pinned array, so
-                               the download overlaps the leaves; 0: a copy engine copies it
-                               back after the sort. The output is the same. */
+  VQ_OPT_HOST_DIRECT = 8    /* host-array sorts of pinned memory: 0 (default): a copy
+                               engine copies the result back after the sort; 1: the leaf
+                               kernels store it straight into the pinned array, so the
+                               download overlaps the leaves (about 8 % faster for one sort
+                               alone, but several times slower while another stream's sort
+                               or upload runs, as the leaves' host stores then contend with
+                               the other work). The output is the same. */
 } vq_option;
 vq_status vqsort_set_option(vq_option opt, int64_t value);
 int64_t vqsort_get_option(vq_option opt);
@@ -273,6 +306,19 @@ vq_status vqsort_profile_reset(void);
    counts (waits for all recorded events). *count gets the entry count. */
 vq_status vqsort_profile_read(const char **names, double *ms, uint64_t *launches, size_t max,
                               size_t *count);
+
+/* Integer throughput probe, a measurement helper (the paper has no
+   counterpart): launches `blocks` blocks of 256 threads on `stream`; each
+   thread updates eight independent registers `iters` times with
+   kind 0: a 32-bit min and an xor (2 lane operations per register and
+   iteration), kind 1: a 64-bit compare, two selects and an xor of both
+   words (6 lane operations), and writes one 32-bit word to d_sink (device
+   memory of blocks * 256 words, caller-owned). *ops_per_thread gets the
+   lane operations per thread. Timed with CUDA events on `stream`, it gives
+   the integer lane-operation rate the leaf networks are measured against.
+   Returns VQ_ERR_INVALID for another kind, zero blocks or null pointers. */
+vq_status vqsort_probe_int_throughput(int kind, unsigned blocks, unsigned iters, void *d_sink,
+                                      uint64_t *ops_per_thread, void *stream);
 
 #ifdef __cplusplus
 }

@@ -44,7 +44,8 @@ class Stats(ctypes.Structure):
         "keys_partitioned", "tiles", "segments", "leaves_warp", "leaves_block", "leaf_keys",
         "equal_ranges", "equal_keys", "degenerate", "fallback_ranges", "fallback_keys",
         "max_depth", "device_status", "keys_counted", "kway_ranges", "guard",
-        "partition_blocks", "leaves_mid", "leaf_ce")]
+        "partition_blocks", "leaves_mid", "leaf_ce", "leaf_keys_warp", "leaf_keys_mid",
+        "leaf_keys_block")]
 
 
 _lib = None
@@ -74,6 +75,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     sigs = {
         "vqsort_sort": ([i32, vp, sz, i32, vp], i32),
         "vqsort_sort_kv": ([vp, sz, i32, vp], i32),
+        "vqsort_sort_kv_by_key": ([vp, sz, i32, vp], i32),
+        "vqsort_sort_kv_by_key_ws": ([vp, sz, i32, vp, sz, vp], i32),
         "vqsort_sort_stable": ([i32, vp, sz, i32, vp, vp], i32),
         "vqsort_sort_host_async": ([i32, vp, sz, i32, vp], i32),
         "vqsort_sort_segmented": ([i32, vp, sz, vp, sz, i32, vp], i32),
@@ -84,6 +87,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "vqsort_partition": ([i32, vp, vp, sz, vp, i32, vp, vp], i32),
         "vqsort_choose_pivot": ([i32, vp, sz, u64, i32, vp, vp], i32),
         "vqsort_last_device_status": ([vp, vp], i32),
+        "vqsort_device_status_async": ([vp, vp, vp], i32),
         "vqsort_get_stats": ([vp, vp, ctypes.POINTER(Stats)], i32),
         "vqsort_status_string": ([i32], ctypes.c_char_p),
         "vqsort_set_option": ([i32, i64], i32),
@@ -92,6 +96,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "vqsort_profile_enable": ([i32], i32),
         "vqsort_profile_reset": ([], i32),
         "vqsort_profile_read": ([vp, vp, vp, sz, ctypes.POINTER(sz)], i32),
+        "vqsort_probe_int_throughput": ([i32, ctypes.c_uint, ctypes.c_uint, vp, ctypes.POINTER(u64), vp], i32),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -170,6 +175,20 @@ def sort_kv_(pairs, descending: bool = False, stream=None):
     _, n = _prep(pairs, "kv64")
     _check(load().vqsort_sort_kv(ctypes.c_void_p(pairs.data_ptr()), n, int(not descending),
                                  _stream(stream)), "vqsort_sort_kv")
+    return pairs
+
+
+def sort_kv_by_key_(pairs, descending: bool = False, stream=None, ws=None):
+    """Sorts (n, 2) 64-bit {key, value} rows in place by key alone (pairs
+    with equal keys in an unspecified order)."""
+    _, n = _prep(pairs, "kv64")
+    if ws is None:
+        _check(load().vqsort_sort_kv_by_key(ctypes.c_void_p(pairs.data_ptr()), n, int(not descending),
+                                            _stream(stream)), "vqsort_sort_kv_by_key")
+    else:
+        p, nb = _ws_ptr(ws)
+        _check(load().vqsort_sort_kv_by_key_ws(ctypes.c_void_p(pairs.data_ptr()), n, int(not descending), p, nb,
+                                               _stream(stream)), "vqsort_sort_kv_by_key_ws")
     return pairs
 
 
@@ -307,6 +326,14 @@ def last_device_status(ws=None, stream=None) -> int:
     return int(load().vqsort_last_device_status(_ws_arg(ws), _stream(stream)))
 
 
+def device_status_async(ws, host_word, stream=None):
+    """Enqueues a copy of workspace `ws`'s device status word into
+    `host_word` (a pinned 1-element int64 CPU tensor) on `stream`; read it
+    once the stream has passed this point (0 = ok)."""
+    _check(load().vqsort_device_status_async(_ws_arg(ws), ctypes.c_void_p(host_word.data_ptr()),
+                                             _stream(stream)), "vqsort_device_status_async")
+
+
 def stats(ws=None, stream=None) -> dict:
     st = Stats()
     _check(load().vqsort_get_stats(_ws_arg(ws), _stream(stream), ctypes.byref(st)), "vqsort_get_stats")
@@ -357,3 +384,31 @@ def profile_read() -> dict:
     la = (ctypes.c_uint64 * k)()
     _check(lib.vqsort_profile_read(names, ms, la, k, ctypes.byref(cnt)), "vqsort_profile_read")
     return {names[i].decode(): {"ms": ms[i], "launches": int(la[i])} for i in range(k)}
+
+
+def probe_int_throughput(kind: int = 0, iters: int = 4096, blocks: int | None = None, reps: int = 5) -> dict:
+    """Times the integer throughput probe (kind 0: 32-bit min, kind 1: 64-bit
+    compare-and-select min) with CUDA events; returns lane operations per
+    second (best of `reps`) and what was run."""
+    torch = _torch()
+    if blocks is None:
+        blocks = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 8
+    sink = torch.empty(blocks * 256, dtype=torch.int32, device="cuda")
+    ops = ctypes.c_uint64(0)
+    s = torch.cuda.current_stream()
+    lib = load()
+    _check(lib.vqsort_probe_int_throughput(kind, blocks, iters, ctypes.c_void_p(sink.data_ptr()),
+                                           ctypes.byref(ops), _stream(s)), "vqsort_probe_int_throughput")
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        _check(lib.vqsort_probe_int_throughput(kind, blocks, iters, ctypes.c_void_p(sink.data_ptr()),
+                                               ctypes.byref(ops), _stream(s)), "vqsort_probe_int_throughput")
+        e1.record(s)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    total = ops.value * blocks * 256
+    return {"lane_ops_per_s": total / (best * 1e-3), "ms": best, "blocks": blocks, "threads": 256,
+            "iters": iters, "ops_per_thread": ops.value}

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libvqsort.so")
 OBJDIR = os.path.join(PKG, "_build")
-SOURCES = ["partition.cu", "leaf.cu", "fallback.cu", "vqsort.cu", "noalloc.cu", "stable.cu"]
+SOURCES = ["partition.cu", "leaf.cu", "fallback.cu", "vqsort.cu", "noalloc.cu", "stable.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

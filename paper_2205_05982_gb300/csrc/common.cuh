@@ -40,6 +40,24 @@ template <> struct KT<16> {   // u128 and kv64: {lo, hi} words
   static __host__ __device__ Code max_code() { return U128{~0ull, ~0ull}; }
 };
 
+// kv64 pairs ordered by the 64-bit key alone (Sec. 2.4: 64-bit keys with
+// 64-bit associated data; Sec. 5: Quicksort is not stable, so pairs with
+// equal keys may come out in any order). The code keeps the value in lo and
+// the key in hi, and every comparison reads hi only. Kernels instantiate
+// this key class as KB = KV_KEYONLY; it occupies 16 bytes of memory.
+struct KV {
+  uint64_t lo, hi;
+};
+constexpr int KV_KEYONLY = 17;
+template <> struct KT<KV_KEYONLY> {
+  using Code = KV;
+  using Mem = U128;
+  static __host__ __device__ Code max_code() { return KV{~0ull, ~0ull}; }
+};
+
+// Bytes a key of class KB occupies in memory.
+__host__ __device__ constexpr int kmem(int kb) { return kb == KV_KEYONLY ? 16 : kb; }
+
 __host__ __device__ __forceinline__ bool lt(uint32_t a, uint32_t b) { return a < b; }
 __host__ __device__ __forceinline__ bool lt(uint64_t a, uint64_t b) { return a < b; }
 // Algorithm 2: the upper word decides unless equal, then the lower word. On
@@ -65,7 +83,9 @@ __host__ __device__ __forceinline__ bool lt(const U128 &a, const U128 &b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 #endif
 }
+__host__ __device__ __forceinline__ bool lt(const KV &a, const KV &b) { return a.hi < b.hi; }
 __host__ __device__ __forceinline__ bool eq(uint32_t a, uint32_t b) { return a == b; }
+__host__ __device__ __forceinline__ bool eq(const KV &a, const KV &b) { return a.hi == b.hi; }
 __host__ __device__ __forceinline__ bool eq(uint64_t a, uint64_t b) { return a == b; }
 __host__ __device__ __forceinline__ bool eq(const U128 &a, const U128 &b) {
   return a.hi == b.hi && a.lo == b.lo;
@@ -90,6 +110,12 @@ __device__ __forceinline__ uint64_t shfl_xor(uint64_t v, int m) { return __shfl_
 __device__ __forceinline__ U128 shfl_xor(const U128 &v, int m) {
   return U128{__shfl_xor_sync(0xFFFFFFFFu, v.lo, m), __shfl_xor_sync(0xFFFFFFFFu, v.hi, m)};
 }
+__device__ __forceinline__ KV shfl_xor(const KV &v, int m) {
+  return KV{__shfl_xor_sync(0xFFFFFFFFu, v.lo, m), __shfl_xor_sync(0xFFFFFFFFu, v.hi, m)};
+}
+__device__ __forceinline__ KV shfl_idx(const KV &v, int l) {
+  return KV{__shfl_sync(0xFFFFFFFFu, v.lo, l), __shfl_sync(0xFFFFFFFFu, v.hi, l)};
+}
 __device__ __forceinline__ uint32_t shfl_idx(uint32_t v, int l) { return __shfl_sync(0xFFFFFFFFu, v, l); }
 __device__ __forceinline__ uint64_t shfl_idx(uint64_t v, int l) { return __shfl_sync(0xFFFFFFFFu, v, l); }
 __device__ __forceinline__ U128 shfl_idx(const U128 &v, int l) {
@@ -103,6 +129,7 @@ __host__ __device__ __forceinline__ uint64_t pred(uint64_t c) { return c - 1; }
 __host__ __device__ __forceinline__ U128 pred(const U128 &c) {
   return U128{c.lo - 1, c.lo == 0 ? c.hi - 1 : c.hi};
 }
+__host__ __device__ __forceinline__ KV pred(const KV &c) { return KV{c.lo, c.hi - 1}; }
 
 // ---------------------------------------------------------------------------
 // Codec: raw key bits <-> code. kind: 0 unsigned, 1 signed integer,
@@ -162,6 +189,18 @@ template <> __host__ __device__ __forceinline__ U128 decode<16>(U128 x, Codec cd
   if (cd.kind == 3) x = U128{x.hi, x.lo};
   return x;
 }
+// Key-only pairs: memory {key, value} -> code {lo = value, hi = key};
+// descending complements the key (the value is complemented too and
+// restored by decode).
+template <> __host__ __device__ __forceinline__ KV encode<KV_KEYONLY>(KV x, Codec cd) {
+  x = KV{x.hi, x.lo};
+  if (cd.desc) x = KV{~x.lo, ~x.hi};
+  return x;
+}
+template <> __host__ __device__ __forceinline__ KV decode<KV_KEYONLY>(KV x, Codec cd) {
+  if (cd.desc) x = KV{~x.lo, ~x.hi};
+  return KV{x.hi, x.lo};
+}
 
 // ---------------------------------------------------------------------------
 // Global memory access for data written by other thread blocks of the same
@@ -181,12 +220,19 @@ template <> __device__ __forceinline__ U128 load_cg<16>(const void *b, uint64_t 
   ulonglong2 v = __ldcg((const ulonglong2 *)b + i);
   return U128{v.x, v.y};
 }
+template <> __device__ __forceinline__ KV load_cg<KV_KEYONLY>(const void *b, uint64_t i) {
+  ulonglong2 v = __ldcg((const ulonglong2 *)b + i);
+  return KV{v.x, v.y};
+}
 
 template <int KB> __device__ __forceinline__ void store_key(void *base, uint64_t i, typename KT<KB>::Code c);
 template <> __device__ __forceinline__ void store_key<2>(void *b, uint64_t i, uint32_t c) { ((uint16_t *)b)[i] = (uint16_t)c; }
 template <> __device__ __forceinline__ void store_key<4>(void *b, uint64_t i, uint32_t c) { ((uint32_t *)b)[i] = c; }
 template <> __device__ __forceinline__ void store_key<8>(void *b, uint64_t i, uint64_t c) { ((uint64_t *)b)[i] = c; }
 template <> __device__ __forceinline__ void store_key<16>(void *b, uint64_t i, U128 c) {
+  ((ulonglong2 *)b)[i] = make_ulonglong2(c.lo, c.hi);
+}
+template <> __device__ __forceinline__ void store_key<KV_KEYONLY>(void *b, uint64_t i, KV c) {
   ((ulonglong2 *)b)[i] = make_ulonglong2(c.lo, c.hi);
 }
 

@@ -168,6 +168,10 @@ cudaError_t launch_fallback(int kb, const SortArgs &a, cudaStream_t s) {
     case 4: return fallback_impl<4>(a, s);
     case 8: return fallback_impl<8>(a, s);
     case 16: return fallback_impl<16>(a, s);
+    // key-only pairs: the merge sort pads with the all-ones code, which ties
+    // with a real key of all ones; it sorts them in the (key, value) order,
+    // one of the orders by key (same bits, same codec)
+    case KV_KEYONLY: return fallback_impl<16>(a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -20,14 +20,14 @@ __host__ __device__ constexpr int part_window(int cpt) { return PART_NT * cpt * 
 __host__ __device__ constexpr int part_smem(int cpt) { return part_window(cpt); }
 // Tile keys: the tile plus its 16-byte misalignment fits the window.
 __host__ __device__ constexpr unsigned part_tile_keys(int kb, int cpt = PART_CPT) {
-  return (unsigned)((part_window(cpt) - 16) / kb);
+  return (unsigned)((part_window(cpt) - 16) / kmem(kb));
 }
 
 // K-way tiles: keys in the first half of the window, the second half stages
 // them in bucket order; at most 16 keys per thread.
-__host__ __device__ constexpr int kw_cpt(int kb, int cpt) { return cpt / 2 < kb ? cpt / 2 : kb; }
+__host__ __device__ constexpr int kw_cpt(int kb, int cpt) { return cpt / 2 < kmem(kb) ? cpt / 2 : kmem(kb); }
 __host__ __device__ constexpr unsigned kw_tile_keys(int kb, int cpt = PART_CPT) {
-  return (unsigned)((PART_NT * kw_cpt(kb, cpt) * 16 - 16) / kb);
+  return (unsigned)((PART_NT * kw_cpt(kb, cpt) * 16 - 16) / kmem(kb));
 }
 
 // Mid-size leaves (more than a warp leaf, at most MID_NT * 16 keys; 16-byte
@@ -35,7 +35,7 @@ __host__ __device__ constexpr unsigned kw_tile_keys(int kb, int cpt = PART_CPT) 
 // many small blocks per SM, and every thread's merge-path search shared by
 // as many keys as its registers hold.
 constexpr int MID_NT = 128;
-__host__ __device__ constexpr unsigned mid_max_keys(int kb) { return kb == 16 ? MID_NT * 8u : MID_NT * 16u; }
+__host__ __device__ constexpr unsigned mid_max_keys(int kb) { return kmem(kb) == 16 ? MID_NT * 8u : MID_NT * 16u; }
 __host__ __device__ constexpr unsigned mid_leaf_limit(int kb) { return mid_max_keys(kb); }
 
 constexpr int LEAF_NT = 1024;       // threads of the block leaf kernel
@@ -64,7 +64,7 @@ __host__ constexpr unsigned default_leaf_cutoff(int kb) {
 __host__ __device__ constexpr unsigned max_leaf_cutoff(int kb) {
   return kb <= 8 ? 16384u : 4096u;   // 16-byte keys: at most 4 per thread in registers
 }
-__host__ constexpr unsigned code_bytes(int kb) { return kb == 2 ? 4u : (unsigned)kb; }
+__host__ constexpr unsigned code_bytes(int kb) { return kb == 2 ? 4u : (unsigned)kmem(kb); }
 
 // Keys per thread for a leaf of len keys on nt threads: the fewest of 4, 8
 // and 16 (at most rmax) that hold it, so that as many threads as possible

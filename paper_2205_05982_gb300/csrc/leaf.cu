@@ -24,8 +24,20 @@ template <int KB> __device__ __forceinline__ typename KT<KB>::Code load_key(cons
   else if constexpr (KB == 8) return ((const uint64_t *)b)[i];
   else {
     const ulonglong2 v = ((const ulonglong2 *)b)[i];
-    return U128{v.x, v.y};
+    return typename KT<KB>::Code{v.x, v.y};
   }
+}
+
+// Key-only pairs (KV) tie on equal keys with different values, so the
+// padding slots and the merge sentinels (all-ones and all-zero codes) must
+// not tie with a real key: a leaf holding a key equal to 0 or 2^64 - 1 is
+// sorted in the (key, value) order instead (the same bits read as a
+// 128-bit code), which is one of the orders by key.
+__device__ __forceinline__ bool edge_key(const KV &c) { return c.hi == 0 || c.hi == ~0ull; }
+template <class C> __device__ __forceinline__ bool edge_key(const C &) { return false; }
+template <int R> __device__ __forceinline__ void as_u128(const KV (&k)[R], U128 (&q)[R]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) q[r] = U128{k[r].lo, k[r].hi};
 }
 
 // Compare-exchanges of the bitonic sorting network on P = G*R keys (G threads
@@ -49,6 +61,23 @@ __device__ __forceinline__ void warp_leaf(const SortArgs &a, const void *src, ui
       k[r] = raw ? encode<KB>(c, a.codec) : c;
     } else {
       k[r] = KT<KB>::max_code();
+    }
+  }
+  if constexpr (KB == KV_KEYONLY) {
+    bool edge = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) edge |= r * 32 + lane < len && edge_key(k[r]);
+    if (__any_sync(0xFFFFFFFFu, edge)) {
+      U128 q[R];
+      as_u128<R>(k, q);
+      warp_sort<U128, R>(q, lane);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const unsigned i = lane * R + r;
+        if (i < len) store_key<16>(a.out, b + i, decode<16>(q[r], a.codec));
+      }
+      if (lane == 0) atomicAdd(&a.hdr->leaf_ce, network_ce<32, R>());
+      return;
     }
   }
   warp_sort<C, R>(k, lane);
@@ -97,6 +126,27 @@ template <int KB, int R> __host__ __device__ constexpr unsigned leaf_run0() {
   return KB <= 4 ? 256u : KB == 8 ? (R >= 16 ? 64u : 128u) : (R >= 8 ? 32u : 64u);
 }
 
+// The keys of one leaf in registers (ns slots on the first nta threads) are
+// sorted by merge_sort_block, staged in shared memory and stored decoded,
+// coalesced, at ob.
+template <int KB, int R, int NT, unsigned L0>
+__device__ __forceinline__ void sort_and_store(const SortArgs &a, typename KT<KB>::Code (&k)[R], unsigned t,
+                                               unsigned len, unsigned ns, unsigned nta,
+                                               typename KT<KB>::Code *sx, void *ob) {
+  using C = typename KT<KB>::Code;
+  merge_sort_block<C, R, NT, L0>(k, t, ns, sx);
+  if (t < nta) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) sx[spad<R>(t * R + r)] = k[r];
+  }
+  __syncthreads();
+  const C *__restrict__ st = sx;
+#pragma unroll 4
+  for (unsigned j = t; j < len; j += NT) store_key<KB>(ob, j, decode<KB>(st[spad<R>(j)], a.codec));
+  if (t == 0) atomicAdd(&a.hdr->leaf_ce, merge_sort_cmps<R, NT, L0>(ns));
+  __syncthreads();
+}
+
 // NT threads sort one range of len <= NT*R keys: the first ns/R threads load
 // the keys (coalesced; ns = len rounded up to the register-stage run),
 // padded with the all-ones code, the last value in sort order (Sec. 2.3);
@@ -111,7 +161,7 @@ __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, u
   const unsigned ns = (len + L0 - 1) / L0 * L0;
   const unsigned nta = ns / R;
   C k[R];
-  const void *sb = (const unsigned char *)src + b * KB;
+  const void *sb = (const unsigned char *)src + b * kmem(KB);
   if (t < nta) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -127,18 +177,19 @@ __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, u
 #pragma unroll
     for (int r = 0; r < R; ++r) k[r] = KT<KB>::max_code();
   }
-  merge_sort_block<C, R, NT, L0>(k, t, ns, sx);
-  if (t < nta) {
+  void *ob = (unsigned char *)a.out + b * kmem(KB);
+  if constexpr (KB == KV_KEYONLY) {
+    bool edge = false;
 #pragma unroll
-    for (int r = 0; r < R; ++r) sx[spad<R>(t * R + r)] = k[r];
+    for (int r = 0; r < R; ++r) edge |= t < nta && r * nta + t < len && edge_key(k[r]);
+    if (__syncthreads_or(edge)) {
+      U128 q[R];
+      as_u128<R>(k, q);
+      sort_and_store<16, R, NT, L0>(a, q, t, len, ns, nta, (U128 *)sx, ob);
+      return;
+    }
   }
-  __syncthreads();
-  const C *__restrict__ st = sx;
-  void *ob = (unsigned char *)a.out + b * KB;
-#pragma unroll 4
-  for (unsigned j = t; j < len; j += NT) store_key<KB>(ob, j, decode<KB>(st[spad<R>(j)], a.codec));
-  if (t == 0) atomicAdd(&a.hdr->leaf_ce, merge_sort_cmps<R, NT, L0>(ns));
-  __syncthreads();
+  sort_and_store<KB, R, NT, L0>(a, k, t, len, ns, nta, sx, ob);
 }
 
 // Starts pulling the keys of leaf `idx` (if it exists) from HBM into L2 with
@@ -152,8 +203,8 @@ __device__ __forceinline__ void prefetch_leaf_l2(const SortArgs &a, const LeafEn
   const LeafEntry le = list[idx];
   if (le.len == 0 || le.begin + le.len > a.n_total) return;
   const uintptr_t src = (uintptr_t)((le.flags & SEG_PARITY) ? a.alt : a.keys);
-  const uintptr_t g0 = (src + le.begin * KB) & ~(uintptr_t)15;
-  const uintptr_t g1 = (src + (le.begin + le.len) * KB + 15) & ~(uintptr_t)15;
+  const uintptr_t g0 = (src + le.begin * kmem(KB)) & ~(uintptr_t)15;
+  const uintptr_t g1 = (src + (le.begin + le.len) * kmem(KB) + 15) & ~(uintptr_t)15;
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g0), "r"((unsigned)(g1 - g0)) : "memory");
 }
 
@@ -207,7 +258,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 && KB <= 8 ? 4 : NT <= 512 ? 2 :
 
 // Mid-size leaves: one MID_NT-thread block per range of (WARP_LEAF_MAX,
 // mid_max_keys(KB)] keys, 8 or 16 keys per thread.
-template <int KB> __global__ void __launch_bounds__(MID_NT, KB == 16 ? 4 : 8) k_leaf_mid(SortArgs a) {
+template <int KB> __global__ void __launch_bounds__(MID_NT, kmem(KB) == 16 ? 4 : 8) k_leaf_mid(SortArgs a) {
   using C = typename KT<KB>::Code;
   constexpr unsigned MAXK = mid_max_keys(KB);
   __shared__ C sx[MAXK + MAXK / 8];
@@ -230,8 +281,8 @@ template <int KB> __global__ void __launch_bounds__(MID_NT, KB == 16 ? 4 : 8) k_
       const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
       const bool raw = le.flags & SEG_RAW;
       const unsigned len = le.len;
-      if (len <= 8 * MID_NT || KB == 16) block_leaf<KB, 8, MID_NT>(a, src, le.begin, len, raw, sx);
-      else block_leaf<KB, (KB == 16 ? 8 : 16), MID_NT>(a, src, le.begin, len, raw, sx);
+      if (len <= 8 * MID_NT || kmem(KB) == 16) block_leaf<KB, 8, MID_NT>(a, src, le.begin, len, raw, sx);
+      else block_leaf<KB, (kmem(KB) == 16 ? 8 : 16), MID_NT>(a, src, le.begin, len, raw, sx);
     }
     __syncthreads();
     idx = s_next;
@@ -281,7 +332,7 @@ template <int KB> int leaf_warp_grid() {
 
 template <int KB> cudaError_t leaf_block_impl(const SortArgs &a, cudaStream_t s) {
   const unsigned C = a.leaf_cutoff < 1024 ? 1024 : a.leaf_cutoff;
-  if constexpr (KB == 16) {   // cutoff <= 4096: at most 8 keys per thread at 512 threads
+  if constexpr (kmem(KB) == 16) {   // cutoff <= 4096: at most 8 keys per thread at 512 threads
     if (a.leaf_threads == 256) {
       const size_t smem = leaf_block_smem(KB, C, 256);
       k_leaf_block<KB, 256><<<leaf_block_grid<KB, 256>(smem), 256, smem, s>>>(a);
@@ -319,6 +370,7 @@ cudaError_t launch_leaf_warp(int kb, const SortArgs &a, cudaStream_t s) {
     case 4: return leaf_warp_impl<4>(a, s);
     case 8: return leaf_warp_impl<8>(a, s);
     case 16: return leaf_warp_impl<16>(a, s);
+    case KV_KEYONLY: return leaf_warp_impl<KV_KEYONLY>(a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -329,6 +381,7 @@ cudaError_t launch_leaf_mid(int kb, const SortArgs &a, cudaStream_t s) {
     case 4: return leaf_mid_impl<4>(a, s);
     case 8: return leaf_mid_impl<8>(a, s);
     case 16: return leaf_mid_impl<16>(a, s);
+    case KV_KEYONLY: return leaf_mid_impl<KV_KEYONLY>(a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -339,6 +392,7 @@ cudaError_t launch_leaf_block(int kb, const SortArgs &a, cudaStream_t s) {
     case 4: return leaf_block_impl<4>(a, s);
     case 8: return leaf_block_impl<8>(a, s);
     case 16: return leaf_block_impl<16>(a, s);
+    case KV_KEYONLY: return leaf_block_impl<KV_KEYONLY>(a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -65,13 +65,16 @@ template <> __device__ __forceinline__ uint64_t key_at<8>(const uint4 &q, unsign
 template <> __device__ __forceinline__ U128 key_at<16>(const uint4 &q, unsigned) {
   return U128{((uint64_t)q.y << 32) | q.x, ((uint64_t)q.w << 32) | q.z};
 }
+template <> __device__ __forceinline__ KV key_at<KV_KEYONLY>(const uint4 &q, unsigned) {
+  return KV{((uint64_t)q.y << 32) | q.x, ((uint64_t)q.w << 32) | q.z};
+}
 
 template <int KB> __device__ __forceinline__ typename KT<KB>::Code code_of(uint64_t lo, uint64_t hi) {
-  if constexpr (KB == 16) return U128{lo, hi};
+  if constexpr (kmem(KB) == 16) return typename KT<KB>::Code{lo, hi};
   else return (typename KT<KB>::Code)lo;
 }
 template <int KB> __device__ __forceinline__ void code_words(typename KT<KB>::Code c, uint64_t &lo, uint64_t &hi) {
-  if constexpr (KB == 16) { lo = c.lo; hi = c.hi; }
+  if constexpr (kmem(KB) == 16) { lo = c.lo; hi = c.hi; }
   else { lo = (uint64_t)c; hi = 0; }
 }
 
@@ -91,11 +94,11 @@ template <int KB>
 __device__ typename KT<KB>::Code sample_pivot(const void *buf, uint64_t b, uint64_t m, bool raw, Codec cd,
                                               uint64_t seed, void *scratch) {
   using C = typename KT<KB>::Code;
-  constexpr unsigned kc = 64 / KB, ns = SAMPLE / kc;
+  constexpr unsigned kc = 64 / kmem(KB), ns = SAMPLE / kc;
   C *s_code = (C *)scratch;
   unsigned long long *s_chunk = (unsigned long long *)(s_code + SAMPLE);
-  const uintptr_t addr = (uintptr_t)buf + b * KB;
-  const uint64_t off = ((64 - (addr & 63)) & 63) / KB;
+  const uintptr_t addr = (uintptr_t)buf + b * kmem(KB);
+  const uint64_t off = ((64 - (addr & 63)) & 63) / kmem(KB);
   const uint64_t nc = (m - off) / kc;
   if (threadIdx.x == 0) {
     Sfc64 r;
@@ -294,10 +297,10 @@ __device__ unsigned long long block_excl_scan(unsigned long long x, unsigned lon
 
 // Keys per thread of the splitter sample: as many as the scratch holds.
 template <int KB, int CPT> __host__ __device__ constexpr unsigned kw_sample_r() {
-  return KB == 16 ? (CPT >= 8 ? 4u : 2u) : (CPT >= 8 ? 8u : 4u);
+  return kmem(KB) == 16 ? (CPT >= 8 ? 4u : 2u) : (CPT >= 8 ? 8u : 4u);
 }
 template <int KB, unsigned R> __host__ __device__ constexpr unsigned kw_scratch_bytes() {
-  return R * NT * (unsigned)sizeof(typename KT<KB>::Code) + R * NT / (64 / KB) * 8u;
+  return R * NT * (unsigned)sizeof(typename KT<KB>::Code) + R * NT / (64 / kmem(KB)) * 8u;
 }
 
 // Leading bits shared by two codes (the code width when they are equal).
@@ -306,6 +309,7 @@ __device__ __forceinline__ unsigned common_prefix(uint64_t x, uint64_t y) { retu
 __device__ __forceinline__ unsigned common_prefix(const U128 &x, const U128 &y) {
   return x.hi != y.hi ? (unsigned)__clzll(x.hi ^ y.hi) : x.lo != y.lo ? 64u + __clzll(x.lo ^ y.lo) : 128u;
 }
+__device__ __forceinline__ unsigned common_prefix(const KV &x, const KV &y) { return common_prefix(x.hi, y.hi); }
 
 // The KW_TABLE_BITS bits of code k that follow its first `sh` bits (zeros
 // past the end of the code); sh is below the code width.
@@ -315,6 +319,7 @@ __device__ __forceinline__ unsigned table_bits(uint32_t k, unsigned sh) {
 __device__ __forceinline__ unsigned table_bits(uint64_t k, unsigned sh) {
   return (unsigned)((k << (sh & 63)) >> (64 - KW_TABLE_BITS));
 }
+__device__ __forceinline__ unsigned table_bits(const KV &k, unsigned sh) { return table_bits(k.hi, sh); }
 __device__ __forceinline__ unsigned table_bits(const U128 &k, unsigned sh) {
   const unsigned s = sh & 127;
   const uint64_t top = s == 0 ? k.hi : s < 64 ? (k.hi << s) | (k.lo >> (64 - s)) : k.lo << (s - 64);
@@ -395,15 +400,15 @@ template <int KB, unsigned R>
 __device__ unsigned build_splitters(const void *buf, uint64_t b, uint64_t m, bool raw, Codec cd, uint64_t seed,
                                     unsigned kbits, KwayDesc &kw, void *scratch) {
   using C = typename KT<KB>::Code;
-  constexpr unsigned S = R * NT, kc = 64 / KB, ns = S / kc;
+  constexpr unsigned S = R * NT, kc = 64 / kmem(KB), ns = S / kc;
   static_assert(S >= 2 * KW_MAX, "sample holds the splitters and their distinct values");
-  constexpr unsigned WIDTH = 8 * sizeof(C);
+  constexpr unsigned WIDTH = KB == KV_KEYONLY ? 64u : 8 * sizeof(C);   // bits the order reads
   C *sx = (C *)scratch;
   unsigned long long *s_chunk = (unsigned long long *)(sx + S);
   __shared__ int s_same;
   __shared__ unsigned long long s_wb[NWARP];
-  const uintptr_t addr = (uintptr_t)buf + b * KB;
-  const uint64_t off = ((64 - (addr & 63)) & 63) / KB;
+  const uintptr_t addr = (uintptr_t)buf + b * kmem(KB);
+  const uint64_t off = ((64 - (addr & 63)) & 63) / kmem(KB);
   const uint64_t nc = (m - off) / kc;
   if (threadIdx.x == 0) {
     Sfc64 r;
@@ -848,7 +853,8 @@ __device__ __forceinline__ bool probe_ticket(const SortArgs &a, unsigned long lo
 }
 
 template <int KB> __device__ __forceinline__ typename KT<KB>::Mem to_mem(typename KT<KB>::Code c) {
-  if constexpr (KB == 16) return c;
+  if constexpr (KB == KV_KEYONLY) return U128{c.lo, c.hi};
+  else if constexpr (KB == 16) return c;
   else return (typename KT<KB>::Mem)c;
 }
 
@@ -860,7 +866,7 @@ __device__ __forceinline__ void count_tile(const SortArgs &a, const uint4 *__res
                                            unsigned hi, typename KT<KB>::Code piv, unsigned &nL,
                                            unsigned &nV, int &anyLt) {
   using C = typename KT<KB>::Code;
-  constexpr unsigned V = 16 / KB;
+  constexpr unsigned V = 16 / kmem(KB);
 #pragma unroll 2
   for (int j = 0; j < CPT; ++j) {
     const unsigned c = threadIdx.x + j * NT;
@@ -868,7 +874,7 @@ __device__ __forceinline__ void count_tile(const SortArgs &a, const uint4 *__res
     const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
 #pragma unroll
     for (unsigned v = 0; v < V; ++v) {
-      const unsigned off = 16 * c + v * KB;
+      const unsigned off = 16 * c + v * kmem(KB);
       const bool valid = full || (off >= lo && off < hi);
       C k = key_at<KB>(q, v);
       if (RAW) k = encode<KB>(k, a.codec);
@@ -888,7 +894,7 @@ __device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *__r
                                              typename KT<KB>::Mem *__restrict__ outR,
                                              unsigned runL, unsigned runR) {
   using C = typename KT<KB>::Code;
-  constexpr unsigned V = 16 / KB;
+  constexpr unsigned V = 16 / kmem(KB);
   const unsigned lane = threadIdx.x & 31;
   const unsigned ltm = (1u << lane) - 1u;
 #pragma unroll 2
@@ -898,7 +904,7 @@ __device__ __forceinline__ void scatter_tile(const SortArgs &a, const uint4 *__r
     const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
 #pragma unroll
     for (unsigned v = 0; v < V; ++v) {
-      const unsigned off = 16 * c + v * KB;
+      const unsigned off = 16 * c + v * kmem(KB);
       const bool valid = full || (off >= lo && off < hi);
       C k = key_at<KB>(q, v);
       if (RAW) k = encode<KB>(k, a.codec);
@@ -927,10 +933,10 @@ __device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *__
                                               unsigned *__restrict__ h0, unsigned *__restrict__ h1,
                                               unsigned char *__restrict__ ids) {
   using C = typename KT<KB>::Code;
-  constexpr unsigned V = 16 / KB;
+  constexpr unsigned V = 16 / kmem(KB);
   constexpr unsigned TK = kw_tile_keys(KB, 2 * KCPT);
-  static_assert(TK * KB == NT * KCPT * 16 - 16, "scatter tile size");
-  const unsigned split = lo + TK * KB;   // first byte of the second scatter tile
+  static_assert(TK * kmem(KB) == NT * KCPT * 16 - 16, "scatter tile size");
+  const unsigned split = lo + TK * kmem(KB);   // first byte of the second scatter tile
 #pragma unroll
   for (int j = 0; j < 2 * KCPT; ++j) {
     const unsigned c = threadIdx.x + j * NT;
@@ -939,14 +945,14 @@ __device__ __forceinline__ void kw_count_tile(const SortArgs &a, const uint4 *__
       const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
 #pragma unroll
       for (unsigned v = 0; v < V; ++v) {
-        const unsigned off = 16 * c + v * KB;
+        const unsigned off = 16 * c + v * kmem(KB);
         if (full || (off >= lo && off < hi)) {
           C k = key_at<KB>(q, v);
           if (RAW) k = encode<KB>(k, a.codec);
           const unsigned bk = cl(k);
           unsigned *h = j < KCPT - 1 ? h0 : j >= KCPT ? h1 : (off < split ? h0 : h1);
           atomicAdd(&h[bk], 1u);
-          ids[(off - lo) / KB] = (unsigned char)bk;   // for the scatter pass
+          ids[(off - lo) / kmem(KB)] = (unsigned char)bk;   // for the scatter pass
         }
       }
     }
@@ -971,7 +977,7 @@ __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *
                                                 unsigned short *__restrict__ s_tstart,
                                                 unsigned *__restrict__ s_off, unsigned long long *s_w) {
   using C = typename KT<KB>::Code;
-  constexpr unsigned V = 16 / KB, Q = KCPT * V;
+  constexpr unsigned V = 16 / kmem(KB), Q = KCPT * V;
   const unsigned tid = threadIdx.x;
   uint32_t pk[Q];   // rank << 8 | bucket, ~0 for no key
 #pragma unroll
@@ -983,9 +989,9 @@ __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *
       const bool full = 16 * c >= lo && 16 * c + 16 <= hi;
 #pragma unroll
       for (unsigned v = 0; v < V; ++v) {
-        const unsigned off = 16 * c + v * KB;
+        const unsigned off = 16 * c + v * kmem(KB);
         if (full || (off >= lo && off < hi)) {
-          const unsigned bk = s_ids[(off - lo) / KB];
+          const unsigned bk = s_ids[(off - lo) / kmem(KB)];
           pk[j * V + v] = (atomicAdd(&s_hist[bk], 1u) << 8) | bk;
         }
       }
@@ -1135,7 +1141,7 @@ __device__ __forceinline__ void issue_tile(const SortArgs &a, unsigned long long
     return;
   }
   const unsigned cnt = (unsigned)min((uint64_t)T, e - t0);
-  const uintptr_t g0 = (uintptr_t)(src + t0 * KB), g1 = g0 + (uintptr_t)cnt * KB;
+  const uintptr_t g0 = (uintptr_t)(src + t0 * kmem(KB)), g1 = g0 + (uintptr_t)cnt * kmem(KB);
   const uintptr_t w0 = g0 & ~(uintptr_t)15, w1 = (g1 + 15) & ~(uintptr_t)15;
   fence_proxy_async_global();
   if ((seg.flags & SEG_KWAY) && (item & ITEM_PHASE)) {
@@ -1191,9 +1197,9 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
   constexpr unsigned TKW = kw_tile_keys(KB, CPT);
   constexpr unsigned RS = kw_sample_r<KB, CPT>();
   static_assert(kw_scratch_bytes<KB, RS>() <= (unsigned)part_window(CPT), "setup sample fits the window");
-  static_assert(2 * TKW * KB + 32 <= (unsigned)part_window(CPT), "a counting tile fits the window");
+  static_assert(2 * TKW * kmem(KB) + 32 <= (unsigned)part_window(CPT), "a counting tile fits the window");
   static_assert(NT == KW_MAX, "one thread per bucket");
-  constexpr unsigned PIV_BYTES = SAMPLE * sizeof(C) + SAMPLE / (64 / KB) * 8;
+  constexpr unsigned PIV_BYTES = SAMPLE * sizeof(C) + SAMPLE / (64 / kmem(KB)) * 8;
   constexpr unsigned LOOKUP_BYTES = KW_MAX * sizeof(C) + KW_TABLE * 2;
   constexpr unsigned AUX = PIV_BYTES > LOOKUP_BYTES ? PIV_BYTES : LOOKUP_BYTES;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1296,7 +1302,7 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
     if (kway && (s_newtree || s_fin)) {
       const KwayDesc &kw = a.kw[sg.piv_lo];
       for (unsigned j = tid; j < KW_MAX; j += NT)
-        s_split[j] = code_of<KB>(__ldcg(&kw.split_lo[j]), KB == 16 ? __ldcg(&kw.split_hi[j]) : 0ull);
+        s_split[j] = code_of<KB>(__ldcg(&kw.split_lo[j]), kmem(KB) == 16 ? __ldcg(&kw.split_hi[j]) : 0ull);
       for (unsigned j = tid; j < KW_TABLE / 2; j += NT)
         ((unsigned *)s_table)[j] = __ldcg((const unsigned *)kw.table + j);
       if (tid == 0) {
@@ -1329,7 +1335,7 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
     M *dst = (M *)(par ? a.keys : a.alt);
     const uint64_t t0 = b + (uint64_t)i * T;
     const unsigned cnt = (unsigned)min((uint64_t)T, e - t0);
-    const uintptr_t g0 = (uintptr_t)(src + t0 * KB), g1 = g0 + (uintptr_t)cnt * KB;
+    const uintptr_t g0 = (uintptr_t)(src + t0 * kmem(KB)), g1 = g0 + (uintptr_t)cnt * kmem(KB);
     const uintptr_t w0 = g0 & ~(uintptr_t)15;
     const unsigned nwc = (unsigned)((((g1 + 15) & ~(uintptr_t)15) - w0) / 16);
     const unsigned lo = (unsigned)(g0 - w0), hi = (unsigned)(g1 - w0);
@@ -1504,6 +1510,7 @@ cudaError_t launch_seed(int kb, const SortArgs &a, cudaStream_t s) {
     case 4: return seed_impl<4>(a, s);
     case 8: return seed_impl<8>(a, s);
     case 16: return seed_impl<16>(a, s);
+    case KV_KEYONLY: return seed_impl<KV_KEYONLY>(a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -1514,6 +1521,7 @@ cudaError_t launch_partition(int kb, const SortArgs &a, cudaStream_t s) {
     case 4: return partition_impl<4>(a, s);
     case 8: return partition_impl<8>(a, s);
     case 16: return partition_impl<16>(a, s);
+    case KV_KEYONLY: return partition_impl<KV_KEYONLY>(a, s);
   }
   return cudaErrorInvalidValue;
 }

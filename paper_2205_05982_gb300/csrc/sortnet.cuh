@@ -35,6 +35,12 @@ template <class C> __device__ __forceinline__ C keep(const C &mine, const C &oth
   const bool take = lt(other, mine) != !lower;
   return take ? other : mine;
 }
+// Key-only pairs tie on equal keys with different values: on a tie both
+// partners keep their own pair, so no pair is lost or duplicated.
+__device__ __forceinline__ KV keep(const KV &mine, const KV &other, bool lower) {
+  const uint64_t x = lower ? other.hi : mine.hi, y = lower ? mine.hi : other.hi;
+  return x < y ? other : mine;
+}
 
 // One merge step. `t` is the thread's index in the sorting group; steps whose
 // partner thread is in another warp go through `sx` (R*NT codes, layout
@@ -120,6 +126,7 @@ template <class C> __device__ __forceinline__ C ones_code();
 template <> __device__ __forceinline__ uint32_t ones_code<uint32_t>() { return ~0u; }
 template <> __device__ __forceinline__ uint64_t ones_code<uint64_t>() { return ~0ull; }
 template <> __device__ __forceinline__ U128 ones_code<U128>() { return U128{~0ull, ~0ull}; }
+template <> __device__ __forceinline__ KV ones_code<KV>() { return KV{~0ull, ~0ull}; }
 
 // Bitonic phases joining runs of L keys up to runs of LEND keys; a run of
 // LEND keys spans LEND/R <= 32 lanes, so every step is a register pairing
@@ -139,6 +146,7 @@ template <class C> __device__ __forceinline__ C zero_code();
 template <> __device__ __forceinline__ uint32_t zero_code<uint32_t>() { return 0u; }
 template <> __device__ __forceinline__ uint64_t zero_code<uint64_t>() { return 0ull; }
 template <> __device__ __forceinline__ U128 zero_code<U128>() { return U128{0ull, 0ull}; }
+template <> __device__ __forceinline__ KV zero_code<KV>() { return KV{0ull, 0ull}; }
 
 // One merge-path round: the ns slots form sorted runs of L keys; afterwards
 // they form sorted runs of 2L. Thread t holds logical slots t*R .. t*R+R-1

@@ -55,7 +55,7 @@ int64_t g_test_stall = 0;
 int64_t g_tile_bytes = 0;     // 0: by key size (tile_cpt)
 int64_t g_leaf_threads = 0;   // 0: 16 keys per thread at the cutoff
 int64_t g_kway = 1;           // K-way levels for ranges of >= 4 x the leaf cutoff
-int64_t g_host_direct = 1;    // host sorts: leaves store into pinned host arrays
+int64_t g_host_direct = 0;    // host sorts: 1 = leaves store into pinned host arrays
 
 // 16-byte chunks per thread of a partition tile window. Default: 64 KiB
 // windows (3 blocks per SM) for 8- and 16-byte keys, 32 KiB (5 per SM) for
@@ -252,6 +252,7 @@ struct Job {
   const void *pivot_host;
   uint64_t *out_left;
   void *out = nullptr;             // sorted keys go here (default: keys)
+  int kclass = 0;                  // kernel key class (0: the key bytes; KV_KEYONLY: pairs by key)
 };
 
 vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
@@ -322,14 +323,15 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
     }
   }
   cudaError_t e;
+  const int kc = j.kclass ? j.kclass : kb;
   if ((e = timed("prep", s, [&] { return launch_prep(a, s); })) != cudaSuccess) return cuda_status(e);
-  if ((e = timed("seed", s, [&] { return launch_seed(kb, a, s); })) != cudaSuccess) return cuda_status(e);
-  if ((e = timed("partition", s, [&] { return launch_partition(kb, a, s); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed("seed", s, [&] { return launch_seed(kc, a, s); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed("partition", s, [&] { return launch_partition(kc, a, s); })) != cudaSuccess) return cuda_status(e);
   if (j.mode == MODE_SORT) {
-    if ((e = timed("leaf_warp", s, [&] { return launch_leaf_warp(kb, a, s); })) != cudaSuccess) return cuda_status(e);
-    if ((e = timed("leaf_mid", s, [&] { return launch_leaf_mid(kb, a, s); })) != cudaSuccess) return cuda_status(e);
-    if ((e = timed("leaf_block", s, [&] { return launch_leaf_block(kb, a, s); })) != cudaSuccess) return cuda_status(e);
-    if ((e = timed("fallback", s, [&] { return launch_fallback(kb, a, s); })) != cudaSuccess) return cuda_status(e);
+    if ((e = timed("leaf_warp", s, [&] { return launch_leaf_warp(kc, a, s); })) != cudaSuccess) return cuda_status(e);
+    if ((e = timed("leaf_mid", s, [&] { return launch_leaf_mid(kc, a, s); })) != cudaSuccess) return cuda_status(e);
+    if ((e = timed("leaf_block", s, [&] { return launch_leaf_block(kc, a, s); })) != cudaSuccess) return cuda_status(e);
+    if ((e = timed("fallback", s, [&] { return launch_fallback(kc, a, s); })) != cudaSuccess) return cuda_status(e);
   }
   return VQ_OK;
 }
@@ -344,7 +346,7 @@ vq_status check_keys(vq_dtype dt, const void *p, uint64_t n) {
 }
 
 vq_status sort_common(vq_dtype dt, void *keys, uint64_t n, const uint64_t *offsets, uint64_t S, int asc,
-                      void *ws, size_t ws_bytes, void *stream) {
+                      void *ws, size_t ws_bytes, void *stream, int kclass = 0) {
   vq_status st = check_keys(dt, keys, n);
   if (st != VQ_OK) return st;
   if (offsets == nullptr && n <= 1) return VQ_OK;
@@ -362,6 +364,7 @@ vq_status sort_common(vq_dtype dt, void *keys, uint64_t n, const uint64_t *offse
     if ((st = owned_ws(s, L.total, &ws, &ws_bytes)) != VQ_OK) return st;
   }
   Job j{dt, keys, nullptr, n, offsets, offsets ? S : 1, asc, MODE_SORT, nullptr, nullptr};
+  j.kclass = kclass;
   return run(j, ws, ws_bytes, s);
 }
 
@@ -455,6 +458,16 @@ vq_status vqsort_sort(vq_dtype dt, void *d_keys, size_t n, int ascending, void *
 
 vq_status vqsort_sort_kv(void *d_pairs, size_t n, int ascending, void *stream) {
   return sort_common(VQ_KV64, d_pairs, n, nullptr, 1, ascending, nullptr, 0, stream);
+}
+
+vq_status vqsort_sort_kv_by_key(void *d_pairs, size_t n, int ascending, void *stream) {
+  return sort_common(VQ_KV64, d_pairs, n, nullptr, 1, ascending, nullptr, 0, stream, KV_KEYONLY);
+}
+
+vq_status vqsort_sort_kv_by_key_ws(void *d_pairs, size_t n, int ascending, void *d_ws, size_t ws_bytes,
+                                   void *stream) {
+  if (!d_ws) return VQ_ERR_INVALID;
+  return sort_common(VQ_KV64, d_pairs, n, nullptr, 1, ascending, d_ws, ws_bytes, stream, KV_KEYONLY);
 }
 
 vq_status vqsort_sort_segmented(vq_dtype dt, void *d_keys, size_t n_total, const uint64_t *d_offsets,
@@ -591,6 +604,13 @@ vq_status vqsort_last_device_status(const void *d_ws, void *stream) {
   return (vq_status)h.error;
 }
 
+vq_status vqsort_device_status_async(const void *d_ws, uint64_t *h_status, void *stream) {
+  if (!d_ws || !h_status) return VQ_ERR_INVALID;
+  const Header *h = (const Header *)d_ws;
+  return cuda_status(cudaMemcpyAsync(h_status, &h->error, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                     (cudaStream_t)stream));
+}
+
 vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out) {
   if (!out) return VQ_ERR_INVALID;
   Header h;
@@ -614,6 +634,9 @@ vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out) {
   out->partition_blocks = h.part_grid;
   out->leaves_mid = h.leaves_mid;
   out->leaf_ce = h.leaf_ce;
+  out->leaf_keys_warp = h.leaf_keys_warp;
+  out->leaf_keys_mid = h.leaf_keys_mid;
+  out->leaf_keys_block = h.leaf_keys_block;
   out->device_status = h.error;
   return VQ_OK;
 }

@@ -45,10 +45,10 @@ def test_status_strings_and_options(lib):
     vq.set_option("depth_limit", 3)
     assert vq.get_option("depth_limit") == 3
     vq.set_option("depth_limit", old)
-    assert vq.get_option("host_direct") == 1      # leaves write pinned arrays by default
-    vq.set_option("host_direct", 0)
-    assert vq.get_option("host_direct") == 0
+    assert vq.get_option("host_direct") == 0      # copy engines bring host results back by default
     vq.set_option("host_direct", 1)
+    assert vq.get_option("host_direct") == 1
+    vq.set_option("host_direct", 0)
     with pytest.raises(vq.VqError):
         vq.set_option("leaf_cutoff", 1000)      # not a power of two
     with pytest.raises(vq.VqError):

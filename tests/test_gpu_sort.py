@@ -224,8 +224,8 @@ def pinned_like(a):
 @pytest.mark.parametrize("ascending", (True, False))
 @pytest.mark.parametrize("direct", (0, 1))
 def test_host_entry_pinned(vq, oracle_mod, dtype, n, dist, ascending, direct):
-    """Pinned host buffers: written by the leaf kernels directly (default),
-    or copied back after the sort (host_direct = 0)."""
+    """Pinned host buffers: copied back after the sort (default), or written
+    by the leaf kernels directly (host_direct = 1)."""
     a = make(dtype, n, dist, seed=n % 101)
     want = oracle_mod.sort(a, dtype, ascending)
     keep, b = pinned_like(a)
@@ -233,7 +233,7 @@ def test_host_entry_pinned(vq, oracle_mod, dtype, n, dist, ascending, direct):
     try:
         vq.sort_host(b, dtype, descending=not ascending)
     finally:
-        vq.set_option("host_direct", 1)
+        vq.set_option("host_direct", 0)
     assert same_bits(b, want)
 
 
@@ -428,7 +428,7 @@ def test_host_async_two_streams(vq, oracle_mod, direct):
     try:
         _host_async_two_streams(vq, oracle_mod, torch)
     finally:
-        vq.set_option("host_direct", 1)
+        vq.set_option("host_direct", 0)
 
 
 def _host_async_two_streams(vq, oracle_mod, torch):
