@@ -52,14 +52,15 @@ def kernel_hash(sources=KERNEL_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(key: str, sources) -> int | None:
-    """DRAM bytes per launch recorded in profiles/traffic.json for `key`, if
-    the kernel's sources still hash to the captured build."""
+def recorded_traffic(key: str, sources, field: str = "bytes_per_launch") -> int | None:
+    """A per-launch ncu figure recorded in profiles/traffic.json for `key`
+    (DRAM bytes, or warp instructions with field="inst_per_launch"), if the
+    kernel's sources still hash to the captured build."""
     try:
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
         if key in tr and tr[key].get("kernel_hash") == kernel_hash(sources):
-            return tr[key]["bytes_per_launch"]
+            return tr[key].get(field)
     except (OSError, ValueError, KeyError):
         pass
     return None
@@ -95,26 +96,39 @@ METRIC = "sort throughput (GKeys/s), 1e8 keys per array"
 
 
 def partition_bytes(kb: int, st: dict) -> int:
-    """Algorithmic bytes of one partition launch: every partitioned key is
-    read and written once (two-way and K-way scatter passes), and K-way
-    ranges read their keys once more in the counting pass."""
-    return kb * (2 * st["keys_partitioned"] + st["keys_counted"])
+    """Algorithmic bytes of one partition launch: every key of every range
+    partitioned at a level is read once and written once (2 x key bytes per
+    key and level, two-way and K-way levels alike)."""
+    return 2 * kb * st["keys_partitioned"]
 
 
-# Integer lane operations of one compare-exchange of two codes: 32-bit codes
-# (2- and 4-byte keys) take a min and a max; 64-bit codes a two-word compare
-# and four selects; 128-bit codes a four-word compare chain and eight selects.
-ALU_OPS_PER_CE = {2: 2, 4: 2, 8: 6, 16: 13}
+def partition_overhead_bytes(kb: int, st: dict) -> dict:
+    """Bytes the K-way levels move beyond the algorithmic ones: the counting
+    pass reads every key once more, and each key's bucket byte is written by
+    the counting pass and read back by the scatter pass."""
+    return {"counting_reread": kb * st["keys_counted"], "bucket_bytes": 2 * st["keys_counted"]}
 
 
-def alu_peak(clk):
-    """Lane operations per second of the integer ALU pipes: SMs x 4 SM
-    sub-partitions x 16 ALU lanes (ncu shows the ALU pipe busier than the
-    issue slots, i.e. a half-rate pipe) x the maximum SM clock."""
-    import torch
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    return sms * 4 * 16 * mhz * 1e6, f"derived: {sms} SMs x 4 sub-partitions x 16 ALU lanes x {mhz:.0f} MHz"
+def leaf_bytes(kb: int, st: dict, kernel: str) -> int:
+    """Algorithmic bytes of one leaf launch: each key of its ranges is read
+    once and written once; the block leaf kernel also copies the all-equal
+    ranges."""
+    keys = {"leaf_warp": st["leaf_keys_warp"], "leaf_mid": st["leaf_keys_mid"],
+            "leaf_block": st["leaf_keys_block"] + st["equal_keys"]}[kernel]
+    return 2 * kb * keys
+
+
+def issue_peak():
+    """Measured integer issue rate of this GPU: the library's throughput
+    probe (eight independent 32-bit min + xor chains per thread, 8 blocks of
+    256 threads per SM), one warp instruction per 32 lane operations."""
+    import paper_2205_05982_gb300 as vq
+    p = vq.probe_int_throughput(kind=0)
+    p64 = vq.probe_int_throughput(kind=1)
+    return {"warp_inst_per_s": p["lane_ops_per_s"] / 32, "lane_ops_per_s": p["lane_ops_per_s"],
+            "min64_per_s": p64["lane_ops_per_s"] / 6,
+            "how": "vqsort_probe_int_throughput kind 0 (32-bit min + xor, 2 lane ops) and kind 1 (64-bit "
+                   "compare + 2 selects + xor, 6 lane ops), CUDA events, best of 5; loop overhead uncounted"}
 
 
 # Nominal HBM3e bandwidth of one GB300 (the measured copy bandwidth is the
@@ -315,11 +329,42 @@ def bits_view(t, torch):
     return t.view({2: torch.int16, 4: torch.int32, 8: torch.int64}[t.element_size()])
 
 
-def time_sorts(vq, torch, copies, ws, dtype, warmup, descending=False):
+def order_codes(t, dtype, torch):
+    """Signed integers whose order is the sort order of the keys in t (same
+    bit patterns; IEEE totalOrder for floats): the check below compares these
+    with torch's own operators. Unsigned keys flip the sign bit; negative
+    floats flip every bit but the sign."""
+    b = bits_view(t.reshape(-1), torch) if dtype not in ("u128", "kv64") else None
+    if dtype in ("u16", "u32", "u64"):
+        return b ^ torch.iinfo(b.dtype).min
+    if dtype in ("f32", "f64"):
+        return b ^ ((b >> (8 * b.element_size() - 1)) & torch.iinfo(b.dtype).max)
+    return b
+
+
+def check_sorted_permutation(out, src, dtype, descending, torch) -> bool:
+    """The output is ordered (codes non-decreasing, or non-increasing when
+    descending) and holds the input's bit patterns as a multiset (equal
+    after sorting both as plain integers with torch.sort)."""
+    if inputs.KEY_BYTES[dtype] == 16:
+        raise ValueError("16-byte keys are checked by the tests")
+    c = order_codes(out, dtype, torch)
+    ok = bool((c[1:] <= c[:-1]).all()) if descending else bool((c[1:] >= c[:-1]).all())
+    bo, bs = bits_view(out.reshape(-1), torch), bits_view(src.reshape(-1), torch)
+    return ok and bool(torch.equal(torch.sort(bo).values, torch.sort(bs).values))
+
+
+def time_sorts(vq, torch, copies, ws, dtype, warmup, descending=False, by_key=False):
     """Sorts copies[0:warmup] untimed, then each remaining copy; returns
-    (ms per sort, stats of the last sort, per-kernel profile)."""
+    (ms per sort, stats of the last sort, per-kernel profile). by_key: kv64
+    pairs in the key-only order (vqsort_sort_kv_by_key_ws)."""
+    def one(c):
+        if by_key:
+            vq.sort_kv_by_key_(c, descending=descending, ws=ws)
+        else:
+            vq.sort_ws_(c, ws, dtype, descending=descending)
     for i in range(warmup):
-        vq.sort_ws_(copies[i], ws, dtype, descending=descending)
+        one(copies[i])
     torch.cuda.synchronize()
     vq.profile_reset()
     vq.profile_enable(True)
@@ -327,7 +372,7 @@ def time_sorts(vq, torch, copies, ws, dtype, warmup, descending=False):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for c in copies[warmup:]:
-        vq.sort_ws_(c, ws, dtype, descending=descending)
+        one(c)
     e1.record()
     torch.cuda.synchronize()
     vq.profile_enable(False)
@@ -358,6 +403,45 @@ def extra_dtypes(vq, torch, peak, n):
     return out
 
 
+def extra_c1(vq, torch, reps=20):
+    """One array of 1e6 uniform u64 keys, ascending, plain path. The array
+    (8 MB) fits in L2, so a 256 MB buffer is written between timed sorts
+    (outside the timed region) and every sort starts from HBM."""
+    n = 1_000_000
+    a = inputs.make("u64", n, "uniform")
+    src = to_device_bits(a, "u64", torch)
+    t = src.clone()
+    ws = vq.alloc_workspace("u64", n)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=src.device)
+    for _ in range(3):
+        t.copy_(src)
+        vq.sort_ws_(t, ws, "u64")
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(reps):
+        t.copy_(src)
+        flush.fill_(i & 255)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        vq.sort_ws_(t, ws, "u64")
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    st = vq.stats(ws)
+    assert st["device_status"] == 0, st
+    assert check_sorted_permutation(t, src, "u64", False, torch)
+    med = statistics.median(ms)
+    res = {"workload": "1e6 uniform u64 keys, one array, ascending (plain path)", "n_keys": n,
+           "gkeys_per_s": n / (med * 1e-3) / 1e9, "us_per_sort": med * 1e3,
+           "us_p10": float(np.percentile(ms, 10)) * 1e3, "us_p90": float(np.percentile(ms, 90)) * 1e3,
+           "sorts": reps, "l2": "256 MB written between timed sorts", "launches_per_sort": 7,
+           "max_depth": st["max_depth"], "kway_ranges": st["kway_ranges"]}
+    del t, src, ws, flush
+    torch.cuda.empty_cache()
+    return res
+
+
 DISTRIBUTIONS = ("uniform", "distinct16", "equal", "sorted", "reverse", "organpipe")
 
 
@@ -382,9 +466,13 @@ def extra_distributions(vq, torch, n):
                 copies = [src.clone() for _ in range(3)]
                 ms, st, _ = time_sorts(vq, torch, copies, ws, dt, 1, descending=desc)
                 assert st["device_status"] == 0, (dt, dist, desc, st)
+                # every timed output: ordered, and a permutation of the input
+                for c in copies:
+                    assert check_sorted_permutation(c, src, dt, desc, torch), (dt, dist, desc)
                 out[f"{dt}:{dist}:{'desc' if desc else 'asc'}"] = {
                     "gkeys_per_s": n / (ms * 1e-3) / 1e9, "ms": ms, "max_depth": st["max_depth"],
-                    "fallback_keys": st["fallback_keys"], "equal_keys": st["equal_keys"]}
+                    "fallback_keys": st["fallback_keys"], "equal_keys": st["equal_keys"],
+                    "outputs_checked": len(copies)}
                 del copies
             del src
         del ws
@@ -396,12 +484,18 @@ def extra_wide(vq, torch, peak, n=25_000_000):
     """Wide keys: 2.5e7 u128 keys (two uniform halves) and 2.5e7 kv64 pairs
     (uniform key, value = index, 10 % of keys duplicated)."""
     out = {}
-    for dt in ("u128", "kv64"):
-        a = inputs.kv_pairs(n) if dt == "kv64" else inputs.make(dt, n, "uniform")
-        src = to_device_bits(a, dt, torch)
+    for dt in ("u128", "kv64", "kv64_by_key"):
+        a = inputs.kv_pairs(n) if dt.startswith("kv64") else inputs.make(dt, n, "uniform")
+        src = to_device_bits(a, "kv64" if dt.startswith("kv64") else dt, torch)
         copies = [src.clone() for _ in range(4)]
-        ws = vq.alloc_workspace(dt, n)
-        ms, st, prof = time_sorts(vq, torch, copies, ws, dt, 1)
+        ws = vq.alloc_workspace("kv64" if dt.startswith("kv64") else dt, n)
+        ms, st, prof = time_sorts(vq, torch, copies, ws, dt[:4], 1, by_key=dt == "kv64_by_key")
+        if dt == "kv64_by_key":   # keys ordered, every value beside its key (value = index)
+            k = copies[-1][:, 0]
+            kc = k ^ torch.iinfo(torch.int64).min
+            assert bool((kc[1:] >= kc[:-1]).all())
+            assert bool(torch.equal(k, src[copies[-1][:, 1], 0]))
+            assert bool(torch.equal(torch.sort(copies[-1][:, 1]).values, src[:, 1]))
         part = prof.get("partition", {"ms": float("nan"), "launches": 1})
         part_ms = part["ms"] / max(1, part["launches"])
         out[dt] = {"gkeys_per_s": n / (ms * 1e-3) / 1e9, "ms": ms,
@@ -538,9 +632,11 @@ def extra_batched(vq, torch, reps=5):
 
 def extra_served(vq, torch, num):
     """Poisson stream of `num` requests, sizes log-uniform in [1e3, 1e7],
-    key type uniform over {i16, u32, f32, u64, kv64}, admitted under a 40 GB
-    budget: saturated capacity, then arrivals at 0.8 x capacity served with
-    continuous batching (8 slots) and one at a time (plain)."""
+    key type uniform over {i16, u32, f32, u64, kv64}, under a 40 GB budget:
+    saturated capacity, then arrivals at 0.8 x capacity served with
+    continuous batching (8 slots, one segmented sort per batch) and one at a
+    time (plain). Every 50th request of the served run is compared, bit for
+    bit, with the same keys sorted alone."""
     from paper_2205_05982_gb300 import serve
     hi = 10_000_000
     sources = {}
@@ -552,13 +648,24 @@ def extra_served(vq, torch, num):
     sat = server.run(burst)
     rate = 0.8 * sat["requests"] / (sat["span_ms"] * 1e-3)
     reqs = serve.poisson_requests(num, rate, sources, seed=6)
+    server.keep_ids = {r.rid for r in reqs[::50]}
     served = server.run(reqs)
+    same = True
+    for r in reqs[::50]:
+        solo = vq.sort(r.source[r.offset:r.offset + r.n].clone(), r.dtype)
+        same &= bool(torch.equal(bits_view(r.out, torch), bits_view(solo, torch)))
+        r.out = None
+    served["identical_output"] = same
+    served["checked_requests"] = len(reqs[::50])
+    del server
     plain = serve.run_plain(serve.poisson_requests(num, rate, sources, seed=6), max_keys=hi)
-    del server, sources
+    del sources
     torch.cuda.empty_cache()
     return {"requests": num, "rate_per_s": rate, "saturated": sat, "served": served, "plain": plain,
-            "p99_speedup": plain["p99_ms"] / served["p99_ms"],
-            "throughput_ratio": served["gkeys_per_s"] / plain["gkeys_per_s"]}
+            "throughput_ratio": served["gkeys_per_s"] / plain["gkeys_per_s"],
+            "p99_ratio": plain["p99_ms"] / served["p99_ms"],
+            "note": "plain is offered the same 0.8 x batched capacity, which exceeds its own, so its "
+                    "latencies include queueing; throughput_ratio is the like-for-like figure"}
 
 
 def run_gpu(args):
@@ -612,23 +719,55 @@ def run_gpu(args):
     ms_total = max_over_ranks(ms_total, dist if world > 1 else None)
     ms_step = ms_total / args.steps
 
-    # spot check: the last timed output is sorted (codes non-decreasing)
-    out = copies[-1]
-    if args.dtype == "u64":
-        enc = out ^ torch.tensor(-2 ** 63, dtype=torch.int64, device=out.device)
-        assert bool((enc[1:] >= enc[:-1]).all())
+    # every timed output is ordered and a permutation of the input
+    if kb != 16:
+        for c in copies[args.warmup:]:
+            assert check_sorted_permutation(c, src, args.dtype, False, torch)
     del copies
 
-    # roofline of the dominant kernel (the persistent partition kernel)
-    part = prof.get("partition", {"ms": float("nan"), "launches": 1})
-    part_ms = part["ms"] / max(1, part["launches"])
-    part_bytes = partition_bytes(kb, st)
+    # rooflines: every kernel's algorithmic bytes per launch (2 x key bytes
+    # per key it partitions or sorts) over its measured time per launch (CUDA
+    # events on the launching stream); the slowest kernel is the dominant one
     peak, peak_kind = hbm_peak()
+
+    def per_launch_ms(name):
+        k = prof.get(name, {"ms": float("nan"), "launches": 1})
+        return k["ms"] / max(1, k["launches"])
+
+    part_ms = per_launch_ms("partition")
+    part_bytes = partition_bytes(kb, st)
     achieved = part_bytes / (part_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(f"{args.dtype}:{args.n}:{args.dist}", KERNEL_SOURCES)
     leaf_ms = sum(v["ms"] for k, v in prof.items() if k.startswith("leaf")) / args.steps
     sort_bytes = part_bytes + 2 * kb * args.n
     ideal = ideal_two_way(kb, args.n, vq.get_option("leaf_cutoff") or DEFAULT_LEAF_CUTOFF[kb])
+    wl = f"{args.dtype}:{args.n}:{args.dist}"
+    rooflines = {"partition": {
+        "bound": "hbm", "kernel": "k_partition (persistent partition levels)", "achieved": achieved,
+        "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+        "traffic": recorded_traffic(wl, KERNEL_SOURCES), "algorithmic_bytes_per_launch": part_bytes,
+        "overhead_bytes_per_launch": partition_overhead_bytes(kb, st), "ms_per_launch": part_ms}}
+    for name in ("leaf_block", "leaf_mid", "leaf_warp"):
+        ms_l = per_launch_ms(name)
+        byts = leaf_bytes(kb, st, name)
+        got = byts / (ms_l * 1e-3) / 1e9 if ms_l > 0 else 0.0
+        rooflines[name] = {"bound": "hbm", "kernel": f"k_{name}", "achieved": got, "peak": peak, "unit": "GB/s",
+                           "frac": got / peak, "peak_source": peak_kind,
+                           "traffic": recorded_traffic(f"{name}:{wl}", LEAF_SOURCES),
+                           "algorithmic_bytes_per_launch": byts, "ms_per_launch": ms_l}
+    # the leaf networks are instruction-bound: their warp instructions per
+    # launch (ncu, recorded) over the measured integer issue rate explain the
+    # HBM fraction
+    ipk = issue_peak()
+    for name in ("leaf_block", "leaf_mid"):
+        inst = recorded_traffic(f"{name}:{wl}", LEAF_SOURCES, "inst_per_launch")
+        r = rooflines[name]
+        r["issue"] = {"inst_per_launch": inst,
+                      "achieved_warp_inst_per_s": inst / (r["ms_per_launch"] * 1e-3) if inst else None,
+                      "peak_warp_inst_per_s": ipk["warp_inst_per_s"],
+                      "frac": inst / (r["ms_per_launch"] * 1e-3) / ipk["warp_inst_per_s"] if inst else None,
+                      "comparisons_per_key": st["leaf_ce"] / max(1, st["leaf_keys"])}
+    dominant = max(rooflines, key=lambda k: rooflines[k]["ms_per_launch"]
+                   if rooflines[k]["ms_per_launch"] == rooflines[k]["ms_per_launch"] else -1)
     kernels = {k: {"ms_per_launch": v["ms"] / max(1, v["launches"]), "launches": v["launches"]}
                for k, v in prof.items()}
     gpu_launches = sum(v["launches"] for v in prof.values())
@@ -638,7 +777,7 @@ def run_gpu(args):
     # alternate between two streams (vqsort_sort_host_async), so one array
     # uploads while the other sorts and writes back over the other direction
     # of the host link. The single synchronous call is reported beside it.
-    e2e_val = e2e_single = e2e_link = None
+    e2e_val = e2e_single = e2e_link = e2e_single_direct = e2e_trials = None
     if not args.no_e2e:
         steps = max(2, args.e2e_steps)
         streams = [torch.cuda.Stream(), torch.cuda.Stream()]
@@ -653,24 +792,40 @@ def run_gpu(args):
             vq.sort_host_async(views[i], args.dtype, stream=streams[i])
         for st_ in streams:
             st_.synchronize()
-        views[0][...] = a
-        views[1][...] = a
-        t0 = time.perf_counter()
-        for i in range(steps):
-            vq.sort_host_async(views[i], args.dtype, stream=streams[i % 2])
-        for st_ in streams:
-            st_.synchronize()
-        t_pipe = time.perf_counter() - t0
-        for st_ in streams:
-            assert vq.last_device_status(None, st_) == 0
-        if args.dtype == "u64":
-            tail = views[-1][: 1 << 20]
-            assert bool((tail[1:] >= tail[:-1]).all())
-        e2e_val = world * args.n * steps / t_pipe / 1e9
-        views[0][...] = a
-        t0 = time.perf_counter()
-        vq.sort_host(views[0], args.dtype)
-        e2e_single = world * args.n / (time.perf_counter() - t0) / 1e9
+        # three trials of the pipelined loop (every array refilled by the CPU
+        # before each trial, outside the timed region); the median is the value
+        trials = []
+        for _ in range(3):
+            for v in views:
+                v[...] = a
+            t0 = time.perf_counter()
+            for i in range(steps):
+                vq.sort_host_async(views[i], args.dtype, stream=streams[i % 2])
+            for st_ in streams:
+                st_.synchronize()
+            trials.append(world * args.n * steps / (time.perf_counter() - t0) / 1e9)
+            for st_ in streams:
+                assert vq.last_device_status(None, st_) == 0
+        if kb != 16:   # the last trial's outputs are ordered
+            for v in views:
+                o = torch.from_numpy(v.view({2: np.int16, 4: np.int32, 8: np.int64}[kb]))
+                c = order_codes(o, args.dtype, torch)
+                assert bool((c[1:] >= c[:-1]).all())
+        e2e_val = statistics.median(trials)
+        # one synchronous call at a time (default copy-back, then the leaves'
+        # direct stores into the pinned array), three calls each, median
+        single, single_direct = [], []
+        for direct, acc in ((0, single), (1, single_direct)):
+            vq.set_option("host_direct", direct)
+            for _ in range(3):
+                views[0][...] = a
+                t0 = time.perf_counter()
+                vq.sort_host(views[0], args.dtype)
+                acc.append(world * args.n / (time.perf_counter() - t0) / 1e9)
+        vq.set_option("host_direct", 0)
+        e2e_single = statistics.median(single)
+        e2e_single_direct = statistics.median(single_direct)
+        e2e_trials = [round(x, 3) for x in trials]
         # the host link of this machine (plain pinned copies of the same size,
         # best of three), to read the end-to-end numbers against
         dev = torch.empty(bufs[0].numel(), dtype=torch.uint8, device=f"cuda:{local}")
@@ -710,12 +865,12 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.dtype, "data": "synthetic",
         "config": workload(args),
-        "roofline": None,   # the dominant kernel's, set below
-        "roofline_partition": {"bound": "hbm", "kernel": "k_partition (persistent partition levels)",
-                               "achieved": achieved, "peak": peak, "unit": "GB/s",
-                               "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
-                               "algorithmic_bytes_per_launch": part_bytes},
-        "sort_roofline": {"bytes_per_step": sort_bytes,
+        "roofline": dict(rooflines[dominant], dominant_of=sorted(rooflines)),
+        "rooflines": rooflines,
+        "issue_peak": ipk,
+        "sort_roofline": {"how": "2 x key bytes x (keys of every partition level actually run + the leaf "
+                                 "pass over all n keys) over the step time",
+                          "bytes_per_step": sort_bytes,
                           "achieved_gbs": sort_bytes / (ms_step * 1e-3) / 1e9,
                           "frac": sort_bytes / (ms_step * 1e-3) / 1e9 / peak,
                           "frac_nominal": sort_bytes / (ms_step * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
@@ -731,28 +886,19 @@ def run_gpu(args):
         "e2e": {"value": e2e_val, "unit": "GKeys/s", "h2d_bytes_per_step": args.n * kb,
                 "d2h_bytes_per_step": args.n * kb,
                 "path": "vqsort_sort_host_async, one pinned host array per step, steps alternating over two "
-                        "streams (upload, sort and write-back of every step inside the timed region)",
-                "single_call": e2e_single, "single_call_path": "vqsort_sort_host (one array, waits)",
+                        "streams (upload, sort and copy-engine write-back of every step inside the timed "
+                        "region); median of 3 trials",
+                "trials": e2e_trials,
+                "single_call": e2e_single, "single_call_path": "vqsort_sort_host (one array, waits; median of 3)",
+                "single_call_leaf_stores": e2e_single_direct,
                 "link": e2e_link},
         "clocks": clk,
     }
-    # the leaf networks: compare-exchanges (counted on the device) x integer
-    # operations per compare-exchange, over the leaf kernels' time
-    apeak, apeak_kind = alu_peak(clk)
-    ce = st["leaf_ce"]
-    leaf_ops = ce * ALU_OPS_PER_CE[kb]
-    leaf_achieved = leaf_ops / (leaf_ms * 1e-3) if leaf_ms > 0 else 0.0
-    line["roofline_leaf"] = {"bound": "alu", "kernel": "k_leaf_warp + k_leaf_mid + k_leaf_block (sorting networks)",
-                             "achieved": leaf_achieved / 1e12, "peak": apeak / 1e12, "unit": "Tlane-op/s",
-                             "frac": leaf_achieved / apeak, "peak_source": apeak_kind,
-                             "traffic": recorded_traffic(f"leaf:{args.dtype}:{args.n}:{args.dist}", LEAF_SOURCES),
-                             "compare_exchanges_per_step": ce, "ops_per_compare_exchange": ALU_OPS_PER_CE[kb]}
-    # the dominant kernel by measured time decides which one is "roofline"
-    line["roofline"] = dict(line["roofline_leaf"] if leaf_ms > part_ms else line["roofline_partition"])
     if rank == 0:
         if not args.no_extras:
             del src
             torch.cuda.empty_cache()
+            line["c1"] = extra_c1(vq, torch)
             line["per_dtype"] = extra_dtypes(vq, torch, peak, args.n)
             line["distributions"] = extra_distributions(vq, torch, args.n)
             line["wide"] = extra_wide(vq, torch, peak)

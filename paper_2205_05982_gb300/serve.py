@@ -1,17 +1,23 @@
 """Serving: a request loop that sorts arrays of different sizes and key
-types as they arrive, with continuous admission.
+types as they arrive, with continuous batching.
 
-Requests arrive over time (`Request.arrival`, seconds from the start). The
-loop admits a request as soon as it has arrived, a slot (a CUDA stream with
-its own resident workspace) is free, and the device-memory budget covers the
-request's key buffer; admitted requests run concurrently on their slots'
-streams, so a request that arrives while others are on the GPU starts
-without waiting for them to finish. Each request sorts its own device buffer
-(filled from a resident source array); its latency is measured from its
-arrival to the completion event of its sort on the GPU clock.
+Requests arrive over time (`Request.arrival`, seconds from the start). Each
+slot owns a CUDA stream and resident device memory: a key arena, a CSR
+offsets buffer and a sort workspace. On every pass of the loop the arrived
+requests are grouped by key type (oldest first); a free slot takes a group
+that fits its arena, copies the keys into it back to back and sorts all of
+them with ONE segmented sort (`vqsort_sort_segmented_ws`: every request is
+a root range of the same on-device recursion, so small requests share the
+partition and leaf launches of large ones). Requests that arrive while
+others are on the GPU join the next batch as soon as a slot frees up, and
+the batches of different slots overlap on the device. A request's latency
+runs from its arrival to the completion event of its batch (GPU clock).
 
-`run_plain` is the comparison: the same arrival stream served one request at
-a time on one stream.
+The device status of every batch is copied into pinned host memory on the
+slot's stream; a batch whose sort latched an error raises when it retires.
+
+`run_plain` is the comparison: the same arrival stream served one request
+at a time on one stream, each with its own plain sort.
 
 Nothing here changes what a sort computes: every request's result is the
 unique sorted order of its keys, alone or in the mix.
@@ -24,7 +30,7 @@ import time
 
 import numpy as np
 
-from . import KEY_BYTES, alloc_workspace, sort_ws_
+from . import KEY_BYTES, STATUS, device_status_async, sort_segmented_ws_, sort_ws_, workspace_bytes
 
 
 @dataclasses.dataclass
@@ -41,106 +47,174 @@ class Request:
     start_ms: float = 0.0
     done_ms: float = 0.0
     latency_ms: float = 0.0
+    batch: int = 0            # requests sorted by the same launch
 
 
 def key_buffer_bytes(r: Request) -> int:
     return r.n * KEY_BYTES[r.dtype]
 
 
+class SortFailed(RuntimeError):
+    pass
+
+
 class Server:
-    """Continuous batching over `slots` streams under `budget_bytes` of device
-    memory (workspaces included)."""
+    """Continuous batching over `slots` streams. Every slot keeps an arena of
+    `arena_keys` keys (16 bytes each, the widest key type), room for
+    `max_segments` requests per batch, and a workspace for the widest key
+    type; all of it stays resident and must fit `budget_bytes`.
+    `segmented=False` sorts every request by itself (one plain sort per
+    request, one request per launch)."""
 
     def __init__(self, slots: int = 8, budget_bytes: int = 40 * 10**9, max_keys: int = 10**7,
-                 keep_outputs: bool = False, device=None):
+                 keep_outputs: bool = False, device=None, arena_keys: int | None = None,
+                 max_segments: int = 512, segmented: bool = True,
+                 dtypes=("i16", "u32", "f32", "u64", "kv64")):
         import torch
         self.torch = torch
         self.device = device or torch.device("cuda")
         self.slots = slots
         self.budget = budget_bytes
         self.keep_outputs = keep_outputs
-        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
-        # one resident workspace per slot, large enough for the biggest request
-        self.ws = [alloc_workspace("kv64", max_keys, 1, device=self.device) for _ in range(slots)]
-        self.ws_bytes = sum(w.numel() for w in self.ws)
-        if self.ws_bytes >= budget_bytes:
-            raise ValueError("budget does not cover the slot workspaces")
+        self.keep_ids: set = set()
+        self.segmented = segmented
         self.max_keys = max_keys
+        self.max_segments = max_segments if segmented else 1
+        self.arena_keys = max(max_keys, arena_keys or 2 * max_keys)
+        arena_bytes = self.arena_keys * 16
+        ws_bytes = max(workspace_bytes(dt, self.arena_keys, self.max_segments) for dt in dtypes) + 256
+        self.resident_bytes = slots * (arena_bytes + ws_bytes + 8 * (self.max_segments + 1))
+        if self.resident_bytes >= budget_bytes:
+            raise ValueError("budget does not cover the slots' arenas and workspaces")
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.arena = [torch.empty(arena_bytes, dtype=torch.uint8, device=self.device) for _ in range(slots)]
+        self.ws = [torch.empty(ws_bytes, dtype=torch.uint8, device=self.device) for _ in range(slots)]
+        self.off_dev = [torch.empty(self.max_segments + 1, dtype=torch.int64, device=self.device)
+                        for _ in range(slots)]
+        self.off_host = [torch.empty(self.max_segments + 1, dtype=torch.int64, pin_memory=True)
+                         for _ in range(slots)]
+        self.status_host = [torch.zeros(1, dtype=torch.int64, pin_memory=True) for _ in range(slots)]
 
-    def _launch(self, r: Request, slot: int, t0_event):
+    def _view(self, slot: int, src, n: int):
+        """The first n keys of the slot's arena, as keys of `src`'s type."""
+        kb = src.element_size() * (src.shape[1] if src.dim() == 2 else 1)
+        v = self.arena[slot][: n * kb].view(src.dtype)
+        return v.reshape(n, 2) if src.dim() == 2 else v
+
+    def _take(self, pending: dict) -> list[Request]:
+        """The next batch: requests of the key type whose oldest request
+        arrived first, in arrival order, while they fit one arena."""
+        dt = min((q[0].arrival, k) for k, q in pending.items() if q)[1]
+        q = pending[dt]
+        group = [q.popleft()]
+        keys, cap = group[0].n, self.arena_keys
+        while q and len(group) < self.max_segments and keys + q[0].n <= cap \
+                and q[0].descending == group[0].descending:
+            keys += q[0].n
+            group.append(q.popleft())
+        return group
+
+    def _launch(self, group: list[Request], slot: int):
         torch = self.torch
         s = self.streams[slot]
+        total = sum(r.n for r in group)
+        src0 = group[0].source
         with torch.cuda.stream(s):
-            if KEY_BYTES[r.dtype] == 16:
-                buf = r.source[r.offset:r.offset + r.n].clone()
-            else:
-                buf = r.source[r.offset:r.offset + r.n].clone()
+            keys = self._view(slot, src0, total)
+            o = 0
+            for r in group:
+                keys[o:o + r.n].copy_(r.source[r.offset:r.offset + r.n])
+                o += r.n
             start = torch.cuda.Event(enable_timing=True)
             done = torch.cuda.Event(enable_timing=True)
             start.record(s)
-            sort_ws_(buf, self.ws[slot], r.dtype, r.descending, s)
+            if self.segmented:
+                offs = np.zeros(len(group) + 1, dtype=np.int64)
+                np.cumsum([r.n for r in group], out=offs[1:])
+                self.off_host[slot][: len(group) + 1].copy_(torch.from_numpy(offs))
+                dev_off = self.off_dev[slot][: len(group) + 1]
+                dev_off.copy_(self.off_host[slot][: len(group) + 1], non_blocking=True)
+                sort_segmented_ws_(keys, dev_off, self.ws[slot], group[0].dtype, group[0].descending, s)
+            else:
+                sort_ws_(keys, self.ws[slot], group[0].dtype, group[0].descending, s)
+            device_status_async(self.ws[slot], self.status_host[slot], s)
+            outs = {}
+            o = 0
+            for r in group:
+                if self.keep_outputs or r.rid in self.keep_ids:
+                    outs[r.rid] = keys[o:o + r.n].clone()
+                o += r.n
             done.record(s)
-        return buf, start, done
+        return start, done, outs
 
     def run(self, requests: list[Request], poll_sleep: float = 20e-6) -> dict:
-        """Serves `requests` (sorted by arrival) and returns latency and
-        throughput statistics. Wall-clock arrival times are honoured."""
+        """Serves `requests` and returns latency and throughput statistics.
+        Wall-clock arrival times are honoured."""
         torch = self.torch
         reqs = sorted(requests, key=lambda r: r.arrival)
         for r in reqs:
             if r.n > self.max_keys:
                 raise ValueError(f"request {r.rid} exceeds max_keys")
-        pending = collections.deque()
+        pending: dict = collections.defaultdict(collections.deque)
         free_slots = list(range(self.slots))
-        inflight = {}   # slot -> (request, buf, start_event, done_event, bytes)
-        used = self.ws_bytes
+        inflight = {}   # slot -> (group, start_event, done_event, outputs)
         nxt = 0
         torch.cuda.synchronize(self.device)
         t0_event = torch.cuda.Event(enable_timing=True)
         t0_event.record(torch.cuda.current_stream(self.device))
         t_start = time.perf_counter()
         finished = []
+        batches = 0
         while len(finished) < len(reqs):
             now = time.perf_counter() - t_start
             while nxt < len(reqs) and reqs[nxt].arrival <= now:
-                pending.append(reqs[nxt])
+                pending[reqs[nxt].dtype].append(reqs[nxt])
                 nxt += 1
-            # admit while a slot is free and memory allows
-            while pending and free_slots and used + key_buffer_bytes(pending[0]) <= self.budget:
-                r = pending.popleft()
+            # admit: one batch per free slot
+            while free_slots and any(pending.values()):
+                group = self._take(pending)
                 slot = free_slots.pop()
-                buf, st, dn = self._launch(r, slot, t0_event)
-                used += key_buffer_bytes(r)
-                inflight[slot] = (r, buf, st, dn, key_buffer_bytes(r))
-            # retire finished work
+                inflight[slot] = (group,) + self._launch(group, slot)
+                batches += 1
+            # retire finished batches
             progressed = False
             for slot in list(inflight):
-                r, buf, st, dn, nbytes = inflight[slot]
+                group, st, dn, outs = inflight[slot]
                 if dn.query():
-                    r.start_ms = t0_event.elapsed_time(st)
-                    r.done_ms = t0_event.elapsed_time(dn)
-                    r.latency_ms = r.done_ms - r.arrival * 1e3
-                    if self.keep_outputs:
-                        r.out = buf
-                    used -= nbytes
+                    status = int(self.status_host[slot].item())
+                    if status != 0:
+                        raise SortFailed(f"batch of {len(group)} {group[0].dtype} requests: device status "
+                                         f"{status} ({STATUS.get(status, status)})")
+                    start_ms, done_ms = t0_event.elapsed_time(st), t0_event.elapsed_time(dn)
+                    for r in group:
+                        r.start_ms, r.done_ms = start_ms, done_ms
+                        r.latency_ms = done_ms - r.arrival * 1e3
+                        r.batch = len(group)
+                        r.out = outs.get(r.rid)
+                        finished.append(r)
                     free_slots.append(slot)
                     del inflight[slot]
-                    finished.append(r)
                     progressed = True
-            if not progressed and (not pending or not free_slots):
-                if nxt < len(reqs) and not inflight and not pending:
+            if not progressed and (not any(pending.values()) or not free_slots):
+                if nxt < len(reqs) and not inflight and not any(pending.values()):
                     wait = reqs[nxt].arrival - (time.perf_counter() - t_start)
                     if wait > 0:
                         time.sleep(min(wait, 1e-3))
                 else:
                     time.sleep(poll_sleep)
         torch.cuda.synchronize(self.device)
-        return summarize(finished)
+        out = summarize(finished)
+        out["batches"] = batches
+        return out
 
 
-def run_plain(requests: list[Request], max_keys: int = 10**7, keep_outputs: bool = False) -> dict:
-    """The same requests served one at a time on one stream, in arrival order."""
-    server = Server(slots=1, max_keys=max_keys, keep_outputs=keep_outputs)
+def run_plain(requests: list[Request], max_keys: int = 10**7, keep_outputs: bool = False,
+              keep_ids=()) -> dict:
+    """The same requests served one at a time on one stream, in arrival
+    order, each by its own plain sort."""
+    server = Server(slots=1, max_keys=max_keys, keep_outputs=keep_outputs, segmented=False,
+                    arena_keys=max_keys)
+    server.keep_ids = set(keep_ids)
     return server.run(requests)
 
 
@@ -155,6 +229,7 @@ def summarize(done: list[Request]) -> dict:
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "span_ms": float(span_ms),
         "gkeys_per_s": keys / (span_ms * 1e-3) / 1e9,
+        "mean_batch": float(np.mean([r.batch for r in done])),
     }
 
 
