@@ -1001,20 +1001,12 @@ __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *
   const unsigned cnt = tid < K ? s_hist[tid] : 0u;
   unsigned long long nkeys;
   const unsigned long long excl = block_excl_scan(cnt, s_w, nkeys);
+  // the bucket's slots are reserved now; the atomic's result is first used
+  // after the staging below, so its round trip overlaps the staging
+  unsigned rel = 0;
   if (tid < K) {
     s_tstart[tid] = (unsigned short)excl;
-    // staged position p of this bucket goes to rbegin + off + p
-    unsigned off = 0;
-    if (cnt) {
-      const unsigned rel = atomicAdd(&kw.cnt[stripe][tid], cnt);
-      if (rbegin + rel + cnt > __ldcg(&kw.start[tid + 1])) {   // guard: stay inside the bucket
-        guard_failed(a, GUARD_BUCKET);
-        off = ~0u;
-      } else {
-        off = rel - (unsigned)excl;   // rel >= excl: earlier buckets fill the tile's first slots
-      }
-    }
-    s_off[tid] = off;
+    if (cnt) rel = atomicAdd(&kw.cnt[stripe][tid], cnt);
     s_hist[tid] = 0;   // ready for the next tile
   }
   __syncthreads();
@@ -1035,6 +1027,19 @@ __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *
         }
       }
     }
+  }
+  if (tid < K) {
+    // staged position p of this bucket goes to rbegin + off + p
+    unsigned off = 0;
+    if (cnt) {
+      if (rbegin + rel + cnt > __ldcg(&kw.start[tid + 1])) {   // guard: stay inside the bucket
+        guard_failed(a, GUARD_BUCKET);
+        off = ~0u;
+      } else {
+        off = rel - (unsigned)excl;   // rel >= excl: earlier buckets fill the tile's first slots
+      }
+    }
+    s_off[tid] = off;
   }
   __syncthreads();
   typename KT<KB>::Mem *__restrict__ out = dst + rbegin;
