@@ -141,8 +141,13 @@ __device__ __forceinline__ void sort_and_store(const SortArgs &a, typename KT<KB
   }
   __syncthreads();
   const C *__restrict__ st = sx;
+  if (KB != KV_KEYONLY && a.codec.kind == 0 && !a.codec.desc) {   // unsigned ascending: codes are the keys
 #pragma unroll 4
-  for (unsigned j = t; j < len; j += NT) store_key<KB>(ob, j, decode<KB>(st[spad<R>(j)], a.codec));
+    for (unsigned j = t; j < len; j += NT) store_key<KB>(ob, j, st[spad<R>(j)]);
+  } else {
+#pragma unroll 4
+    for (unsigned j = t; j < len; j += NT) store_key<KB>(ob, j, decode<KB>(st[spad<R>(j)], a.codec));
+  }
   if (t == 0) atomicAdd(&a.hdr->leaf_ce, merge_sort_cmps<R, NT, L0>(ns));
   __syncthreads();
 }
@@ -162,16 +167,17 @@ __device__ __forceinline__ void block_leaf(const SortArgs &a, const void *src, u
   const unsigned nta = ns / R;
   C k[R];
   const void *sb = (const unsigned char *)src + b * kmem(KB);
-  if (t < nta) {
+  if (t < nta && !raw) {   // keys written by a partition level are codes already
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const unsigned j = r * nta + t;
-      if (j < len) {
-        C c = load_key<KB>(sb, j);
-        k[r] = raw ? encode<KB>(c, a.codec) : c;
-      } else {
-        k[r] = KT<KB>::max_code();
-      }
+      k[r] = j < len ? load_key<KB>(sb, j) : KT<KB>::max_code();
+    }
+  } else if (t < nta) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const unsigned j = r * nta + t;
+      k[r] = j < len ? encode<KB>(load_key<KB>(sb, j), a.codec) : KT<KB>::max_code();
     }
   } else {
 #pragma unroll
