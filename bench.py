@@ -135,7 +135,7 @@ def issue_peak():
 # main denominator; this one is reported beside it).
 NOMINAL_HBM_GBS = 8000.0
 # Leaf cutoff the library uses by key size when none is set.
-DEFAULT_LEAF_CUTOFF = {2: 4096, 4: 4096, 8: 8192, 16: 4096}
+DEFAULT_LEAF_CUTOFF = {2: 4096, 4: 4096, 8: 4096, 16: 4096}
 
 
 def ideal_two_way(kb: int, n: int, cutoff: int) -> dict:
@@ -577,9 +577,11 @@ def extra_partition_sweep(vq, torch, peak, reps=10):
 
 
 def extra_batched(vq, torch, reps=5):
-    """16,384 arrays, sizes log-uniform in [16, 65536], uniform u32 keys:
-    one autotuned segmented sort replayed as a CUDA graph vs one plain sort
-    launch set per array. Outputs are compared byte for byte."""
+    """16,384 arrays, sizes log-uniform in [16, 65536], uniform u32 / f32
+    keys: one autotuned segmented sort replayed as a CUDA graph vs one plain
+    sort launch set per array, issued from Python and, without that
+    overhead, captured into one CUDA graph. Outputs are compared byte for
+    byte."""
     from paper_2205_05982_gb300 import batch
     res = {}
     for dt in ("u32", "f32"):
@@ -617,10 +619,29 @@ def extra_batched(vq, torch, reps=5):
             e1.record()
             torch.cuda.synchronize()
             p_ms.append(e0.elapsed_time(e1))
+        # the same per-array launches captured into one CUDA graph: the
+        # baseline without Python and launch overhead
+        eg = src.clone()
+        pg, pstream = batch.capture_each(eg, off, dt, ws1)
+        pg_ms = []
+        for _ in range(max(1, reps // 2)):
+            eg.copy_(src)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(pstream)
+            with torch.cuda.stream(pstream):
+                pg.replay()
+            e1.record(pstream)
+            torch.cuda.synchronize()
+            pg_ms.append(e0.elapsed_time(e1))
         # bit patterns (f32 holds NaNs, which never compare equal as floats)
-        same = bool(torch.equal(bits_view(graph_out, torch), bits_view(each, torch)))
-        gm, pm = float(np.median(g_ms)), float(np.median(p_ms))
+        same = bool(torch.equal(bits_view(graph_out, torch), bits_view(each, torch))) and \
+            bool(torch.equal(bits_view(graph_out, torch), bits_view(eg, torch)))
+        gm, pm, pgm = float(np.median(g_ms)), float(np.median(p_ms)), float(np.median(pg_ms))
+        del pg, eg
         res[dt] = {"arrays": int(sizes.size), "keys": n, "graph_ms": gm, "per_array_ms": pm,
+                   "per_array_graph_ms": pgm, "speedup_vs_per_array_graph": pgm / gm,
                    "graph_gkeys_per_s": n / (gm * 1e-3) / 1e9,
                    "per_array_gkeys_per_s": n / (pm * 1e-3) / 1e9, "speedup": pm / gm,
                    "identical_output": same, "tuned": tune["settings"],
@@ -628,6 +649,9 @@ def extra_batched(vq, torch, reps=5):
         del b, src, each
         torch.cuda.empty_cache()
     return res
+
+
+FIXED_RATE = 7500.0
 
 
 def extra_served(vq, torch, num):
@@ -657,11 +681,15 @@ def extra_served(vq, torch, num):
         r.out = None
     served["identical_output"] = same
     served["checked_requests"] = len(reqs[::50])
+    # latency at a fixed arrival rate (7,500 requests/s), comparable across
+    # builds whose saturated capacity differs
+    fixed = server.run(serve.poisson_requests(num, FIXED_RATE, sources, seed=6))
     del server
     plain = serve.run_plain(serve.poisson_requests(num, rate, sources, seed=6), max_keys=hi)
     del sources
     torch.cuda.empty_cache()
     return {"requests": num, "rate_per_s": rate, "saturated": sat, "served": served, "plain": plain,
+            "fixed_rate": dict(fixed, rate_per_s=FIXED_RATE),
             "throughput_ratio": served["gkeys_per_s"] / plain["gkeys_per_s"],
             "p99_ratio": plain["p99_ms"] / served["p99_ms"],
             "note": "plain is offered the same 0.8 x batched capacity, which exceeds its own, so its "
@@ -777,7 +805,7 @@ def run_gpu(args):
     # alternate between two streams (vqsort_sort_host_async), so one array
     # uploads while the other sorts and writes back over the other direction
     # of the host link. The single synchronous call is reported beside it.
-    e2e_val = e2e_single = e2e_link = e2e_single_direct = e2e_trials = None
+    e2e_val = e2e_single = e2e_link = e2e_single_direct = e2e_trials = e2e_cpu = None
     if not args.no_e2e:
         steps = max(2, args.e2e_steps)
         streams = [torch.cuda.Stream(), torch.cuda.Stream()]
@@ -792,25 +820,46 @@ def run_gpu(args):
             vq.sort_host_async(views[i], args.dtype, stream=streams[i])
         for st_ in streams:
             st_.synchronize()
-        # three trials of the pipelined loop (every array refilled by the CPU
-        # before each trial, outside the timed region); the median is the value
-        trials = []
-        for _ in range(3):
+        # Inputs are staged into the pinned arrays before each trial, outside
+        # the timed region, by a copy from the device-resident input (a DMA
+        # write): on these machines pinned pages the CPU has just written are
+        # slow for any GPU transfer, and more so the longer ago they were
+        # written (plain copies of such arrays ran at 25-140 GB/s against
+        # 340 GB/s otherwise), which is a property of the host, not of the
+        # sort. The same loop on CPU-written arrays is reported beside it.
+        src_bytes = src.reshape(-1).view(torch.uint8)
+
+        def stage_gpu():
+            for b in bufs:
+                b.copy_(src_bytes, non_blocking=True)
+            torch.cuda.synchronize()
+
+        def stage_cpu():
             for v in views:
                 v[...] = a
+
+        def pipelined():
             t0 = time.perf_counter()
             for i in range(steps):
                 vq.sort_host_async(views[i], args.dtype, stream=streams[i % 2])
             for st_ in streams:
                 st_.synchronize()
-            trials.append(world * args.n * steps / (time.perf_counter() - t0) / 1e9)
             for st_ in streams:
                 assert vq.last_device_status(None, st_) == 0
+            return world * args.n * steps / (time.perf_counter() - t0) / 1e9
+
+        trials, cpu_trials = [], []
+        for _ in range(3):
+            stage_gpu()
+            trials.append(pipelined())
         if kb != 16:   # the last trial's outputs are ordered
             for v in views:
                 o = torch.from_numpy(v.view({2: np.int16, 4: np.int32, 8: np.int64}[kb]))
                 c = order_codes(o, args.dtype, torch)
                 assert bool((c[1:] >= c[:-1]).all())
+        for _ in range(2):
+            stage_cpu()
+            cpu_trials.append(pipelined())
         e2e_val = statistics.median(trials)
         # one synchronous call at a time (default copy-back, then the leaves'
         # direct stores into the pinned array), three calls each, median
@@ -818,7 +867,8 @@ def run_gpu(args):
         for direct, acc in ((0, single), (1, single_direct)):
             vq.set_option("host_direct", direct)
             for _ in range(3):
-                views[0][...] = a
+                bufs[0].copy_(src_bytes)
+                torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 vq.sort_host(views[0], args.dtype)
                 acc.append(world * args.n / (time.perf_counter() - t0) / 1e9)
@@ -826,6 +876,7 @@ def run_gpu(args):
         e2e_single = statistics.median(single)
         e2e_single_direct = statistics.median(single_direct)
         e2e_trials = [round(x, 3) for x in trials]
+        e2e_cpu = [round(x, 3) for x in cpu_trials]
         # the host link of this machine (plain pinned copies of the same size,
         # best of three), to read the end-to-end numbers against
         dev = torch.empty(bufs[0].numel(), dtype=torch.uint8, device=f"cuda:{local}")
@@ -848,12 +899,25 @@ def run_gpu(args):
         d2h_ms = [copy_ms(b, dev) for b in bufs]
         nbytes = bufs[0].numel()
         h2d_med, d2h_med = statistics.median(h2d_ms), statistics.median(d2h_ms)
+        # the first upload of each array right after the CPU rewrote them all
+        stage_cpu()
+        cpu_h2d = []
+        for b in bufs:
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record()
+            dev.copy_(b, non_blocking=True)
+            c1.record()
+            c1.synchronize()
+            cpu_h2d.append(round(b.numel() / c0.elapsed_time(c1) / 1e6, 1))
         e2e_link = {"h2d_gbs": nbytes / h2d_med / 1e6, "d2h_gbs": nbytes / d2h_med / 1e6,
                     "copy_only_gkeys_per_s": args.n / ((h2d_med + d2h_med) * 1e-3) / 1e9,
                     "per_array_h2d_gbs": [round(nbytes / t / 1e6, 1) for t in h2d_ms],
                     "per_array_d2h_gbs": [round(nbytes / t / 1e6, 1) for t in d2h_ms],
+                    "per_array_h2d_gbs_cpu_filled": cpu_h2d,
                     "how": "each pinned array of the timed loop up, then down, no sort (CUDA events, "
-                           "best of 3 per array; the scalar rates are the medians)"}
+                           "best of 3 per array; the scalar rates are the medians); cpu_filled: one upload "
+                           "of each array right after the CPU rewrote all of them"}
         del dev, bufs, views
 
     line = {
@@ -887,8 +951,11 @@ def run_gpu(args):
                 "d2h_bytes_per_step": args.n * kb,
                 "path": "vqsort_sort_host_async, one pinned host array per step, steps alternating over two "
                         "streams (upload, sort and copy-engine write-back of every step inside the timed "
-                        "region); median of 3 trials",
+                        "region); inputs staged into the pinned arrays by a device-to-host copy before each "
+                        "trial; median of 3 trials",
                 "trials": e2e_trials,
+                "cpu_filled_trials": e2e_cpu,
+                "cpu_filled_note": "the same loop right after the CPU rewrote every pinned array",
                 "single_call": e2e_single, "single_call_path": "vqsort_sort_host (one array, waits; median of 3)",
                 "single_call_leaf_stores": e2e_single_direct,
                 "link": e2e_link},

@@ -55,11 +55,11 @@ __host__ constexpr int leaf_nt_for(unsigned cutoff, int threads) {
 
 // Default and largest block-leaf cutoff (keys) per key size. The default
 // also sets the K-way bucket target (a quarter of it); measured on 1e8-key
-// sorts, 4096 is best for 2- and 4-byte keys (u32 3.01 -> 2.37 ms against
-// 16384: buckets of ~1K keys fit the 128-thread leaves) and 8192 for 8-byte
-// keys.
+// sorts, 4096 is best for every key size (u32 3.01 -> 2.37 ms against
+// 16384; u64 3.38 -> 3.24 ms against 8192: block leaves then run on 256
+// threads with 16 keys each, one code path).
 __host__ constexpr unsigned default_leaf_cutoff(int kb) {
-  return kb == 2 ? 4096u : kb == 4 ? 4096u : kb == 8 ? 8192u : 4096u;
+  return kb == 2 ? 4096u : kb == 4 ? 4096u : kb == 8 ? 4096u : 4096u;
 }
 __host__ __device__ constexpr unsigned max_leaf_cutoff(int kb) {
   return kb <= 8 ? 16384u : 4096u;   // 16-byte keys: at most 4 per thread in registers

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 && KB <= 8 ? 4 : NT <= 512 ? 2 :
 }
 
 // Mid-size leaves: one MID_NT-thread block per range of (WARP_LEAF_MAX,
-// mid_max_keys(KB)] keys, 8 or 16 keys per thread.
+// mid_max_keys(KB)] keys, 16 keys per thread (16-byte keys: 8).
 template <int KB> __global__ void __launch_bounds__(MID_NT, kmem(KB) == 16 ? 4 : 8) k_leaf_mid(SortArgs a) {
   using C = typename KT<KB>::Code;
   constexpr unsigned MAXK = mid_max_keys(KB);
@@ -287,8 +287,9 @@ template <int KB> __global__ void __launch_bounds__(MID_NT, kmem(KB) == 16 ? 4 :
       const void *src = (le.flags & SEG_PARITY) ? a.alt : a.keys;
       const bool raw = le.flags & SEG_RAW;
       const unsigned len = le.len;
-      if (len <= 8 * MID_NT || kmem(KB) == 16) block_leaf<KB, 8, MID_NT>(a, src, le.begin, len, raw, sx);
-      else block_leaf<KB, (kmem(KB) == 16 ? 8 : 16), MID_NT>(a, src, le.begin, len, raw, sx);
+      // one register count per key size: a second instantiation of the
+      // sort doubled the code the instruction cache has to hold
+      block_leaf<KB, (kmem(KB) == 16 ? 8 : 16), MID_NT>(a, src, le.begin, len, raw, sx);
     }
     __syncthreads();
     idx = s_next;

@@ -131,13 +131,41 @@ template <> __device__ __forceinline__ KV ones_code<KV>() { return KV{~0ull, ~0u
 // Bitonic phases joining runs of L keys up to runs of LEND keys; a run of
 // LEND keys spans LEND/R <= 32 lanes, so every step is a register pairing
 // or a shuffle.
+//
+// The phases run as a loop over three step bodies, not unrolled per phase
+// (which multiplied the code and made the leaves wait on the instruction
+// cache): a phase joining runs of L keys is one mirrored exchange with the
+// lane 2L/R - 1 away (register r against R - 1 - r), exchanges with the
+// lanes L/(2R), ..., 1 away, and the log2(R) steps inside each thread's
+// registers (vq_merge_step gives the same schedule).
 template <class C, int R, unsigned L, unsigned LEND>
 __device__ __forceinline__ void warp_phases(C (&k)[R], unsigned lane) {
-  if constexpr (L < LEND) {
-    constexpr unsigned steps = ilog2(L) + 1;
+#pragma unroll 1
+  for (unsigned l = L; l < LEND; l *= 2) {
+    {   // step 0: mirrored partner, lower half of each 2l block keeps the minimum
+      const unsigned lx = 2 * l / R - 1;
+      const bool lower = (lane & (l / R)) == 0;
 #pragma unroll
-    for (unsigned s = 0; s < steps; ++s) merge_step<C, R, 32>(k, vq_merge_step(L, R, s), lane, nullptr);
-    warp_phases<C, R, 2 * L, LEND>(k, lane);
+      for (int r = 0; r < (R + 1) / 2; ++r) {
+        const C o1 = shfl_xor(k[R - 1 - r], (int)lx);
+        const C o2 = shfl_xor(k[r], (int)lx);
+        k[r] = keep(k[r], o1, lower);
+        if (R - 1 - r != r) k[R - 1 - r] = keep(k[R - 1 - r], o2, lower);
+      }
+    }
+#pragma unroll 1
+    for (unsigned d = l / 2; d >= (unsigned)R; d /= 2) {   // partners d/R lanes away
+      const unsigned lx = d / R;
+      const bool lower = (lane & lx) == 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) k[r] = keep(k[r], shfl_xor(k[r], (int)lx), lower);
+    }
+#pragma unroll
+    for (int dr = R / 2; dr >= 1; dr /= 2) {   // partners inside the thread
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if ((r & dr) == 0) cas(k[r], k[r ^ dr]);
+    }
   }
 }
 
