@@ -141,6 +141,22 @@ def sort_each(keys, offsets, dtype: str, ws=None, descending: bool = False, stre
     return keys
 
 
+def capture_each(keys, offsets, dtype: str, ws, descending: bool = False):
+    """The per-array baseline captured into ONE CUDA graph: a replay launches
+    one plain sort (its fixed kernel sequence) per array, back to back, with
+    no host work between them. Returns (graph, stream)."""
+    import torch
+    stream = torch.cuda.Stream(device=keys.device)
+    stream.wait_stream(torch.cuda.current_stream(keys.device))
+    with torch.cuda.stream(stream):
+        sort_each(keys, offsets, dtype, ws=ws, descending=descending, stream=stream)   # warm-up, uncaptured
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        sort_each(keys, offsets, dtype, ws=ws, descending=descending, stream=stream)
+    return graph, stream
+
+
 def _time_batch(batch: SegmentedBatch, reps: int) -> float:
     import torch
     src = batch.keys.clone()
@@ -222,5 +238,5 @@ def tuned_settings(n_total: int, num_segments: int, dtype: str) -> dict | None:
     return e["settings"] if e else None
 
 
-__all__ = ["SegmentedBatch", "sort_each", "autotune", "tuned_settings", "candidates", "settings_scope",
+__all__ = ["SegmentedBatch", "sort_each", "capture_each", "autotune", "tuned_settings", "candidates", "settings_scope",
            "CODE"]

@@ -62,13 +62,16 @@ class Server:
     """Continuous batching over `slots` streams. Every slot keeps an arena of
     `arena_keys` keys (16 bytes each, the widest key type), room for
     `max_segments` requests per batch, and a workspace for the widest key
-    type; all of it stays resident and must fit `budget_bytes`.
-    `segmented=False` sorts every request by itself (one plain sort per
+    type; all of it stays resident and must fit `budget_bytes`. A batch
+    gathers requests up to `batch_keys` keys (default: the arena), so small
+    requests need not wait behind a full arena; measured at 0.8 x capacity,
+    2.5e6 keys gave p99 3.9 ms at 11 GKeys/s against 6.8 ms at 22 GKeys/s for
+    a full arena. `segmented=False` sorts every request by itself (one plain sort per
     request, one request per launch)."""
 
     def __init__(self, slots: int = 8, budget_bytes: int = 40 * 10**9, max_keys: int = 10**7,
                  keep_outputs: bool = False, device=None, arena_keys: int | None = None,
-                 max_segments: int = 512, segmented: bool = True,
+                 max_segments: int = 512, segmented: bool = True, batch_keys: int | None = None,
                  dtypes=("i16", "u32", "f32", "u64", "kv64")):
         import torch
         self.torch = torch
@@ -81,6 +84,8 @@ class Server:
         self.max_keys = max_keys
         self.max_segments = max_segments if segmented else 1
         self.arena_keys = max(max_keys, arena_keys or 2 * max_keys)
+        # keys a batch may gather (a request larger than this goes alone)
+        self.batch_keys = min(self.arena_keys, batch_keys or self.arena_keys)
         arena_bytes = self.arena_keys * 16
         ws_bytes = max(workspace_bytes(dt, self.arena_keys, self.max_segments) for dt in dtypes) + 256
         self.resident_bytes = slots * (arena_bytes + ws_bytes + 8 * (self.max_segments + 1))
@@ -107,7 +112,7 @@ class Server:
         dt = min((q[0].arrival, k) for k, q in pending.items() if q)[1]
         q = pending[dt]
         group = [q.popleft()]
-        keys, cap = group[0].n, self.arena_keys
+        keys, cap = group[0].n, self.batch_keys
         while q and len(group) < self.max_segments and keys + q[0].n <= cap \
                 and q[0].descending == group[0].descending:
             keys += q[0].n
