@@ -82,6 +82,9 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the per-dtype, batched and served measurements")
     p.add_argument("--served-requests", type=int, default=10_000)
+    p.add_argument("--leaf-sizes", default=None,
+                   help="LO,HI: leaf microbenchmark instead: --n keys in segments of LO..HI keys (each at most "
+                        "the leaf cutoff, so every segment goes straight to a leaf kernel)")
     return p.parse_args()
 
 
@@ -119,9 +122,10 @@ def leaf_bytes(kb: int, st: dict, kernel: str) -> int:
 
 
 def issue_peak():
-    """Measured integer issue rate of this GPU: the library's throughput
+    """Measured integer ALU-pipe rate of this GPU: the library's throughput
     probe (eight independent 32-bit min + xor chains per thread, 8 blocks of
-    256 threads per SM), one warp instruction per 32 lane operations."""
+    256 threads per SM; both instructions run on the ALU pipe), one warp
+    instruction per 32 lane operations."""
     import paper_2205_05982_gb300 as vq
     p = vq.probe_int_throughput(kind=0)
     p64 = vq.probe_int_throughput(kind=1)
@@ -782,18 +786,21 @@ def run_gpu(args):
                            "frac": got / peak, "peak_source": peak_kind,
                            "traffic": recorded_traffic(f"{name}:{wl}", LEAF_SOURCES),
                            "algorithmic_bytes_per_launch": byts, "ms_per_launch": ms_l}
-    # the leaf networks are instruction-bound: their warp instructions per
-    # launch (ncu, recorded) over the measured integer issue rate explain the
-    # HBM fraction
+    # the leaf sorts are bound by the integer ALU pipe: their ALU-pipe warp
+    # instructions per launch (ncu, recorded) over the measured ALU-pipe
+    # rate of the throughput probe explain the low HBM fraction
     ipk = issue_peak()
     for name in ("leaf_block", "leaf_mid"):
+        alu = recorded_traffic(f"{name}:{wl}", LEAF_SOURCES, "alu_inst_per_launch")
         inst = recorded_traffic(f"{name}:{wl}", LEAF_SOURCES, "inst_per_launch")
         r = rooflines[name]
-        r["issue"] = {"inst_per_launch": inst,
-                      "achieved_warp_inst_per_s": inst / (r["ms_per_launch"] * 1e-3) if inst else None,
-                      "peak_warp_inst_per_s": ipk["warp_inst_per_s"],
-                      "frac": inst / (r["ms_per_launch"] * 1e-3) / ipk["warp_inst_per_s"] if inst else None,
-                      "comparisons_per_key": st["leaf_ce"] / max(1, st["leaf_keys"])}
+        keys = r["algorithmic_bytes_per_launch"] / (2 * kb)
+        r["alu"] = {"alu_inst_per_launch": alu, "inst_per_launch": inst,
+                    "thread_inst_per_key": inst * 32 / keys if inst and keys else None,
+                    "achieved_alu_inst_per_s": alu / (r["ms_per_launch"] * 1e-3) if alu else None,
+                    "peak_alu_inst_per_s": ipk["warp_inst_per_s"],
+                    "frac": alu / (r["ms_per_launch"] * 1e-3) / ipk["warp_inst_per_s"] if alu else None,
+                    "comparisons_per_key": st["leaf_ce"] / max(1, st["leaf_keys"])}
     dominant = max(rooflines, key=lambda k: rooflines[k]["ms_per_launch"]
                    if rooflines[k]["ms_per_launch"] == rooflines[k]["ms_per_launch"] else -1)
     kernels = {k: {"ms_per_launch": v["ms"] / max(1, v["launches"]), "launches": v["launches"]}
@@ -979,10 +986,57 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_leaf_sizes(args):
+    """Leaf microbenchmark: --n uniform keys of --dtype in CSR segments whose
+    lengths are drawn uniformly from [LO, HI] (seeded); one segmented sort
+    per step. Every segment is at most the leaf cutoff, so the sort is the
+    leaf kernels alone (the partition kernel finds no work). Prints per-kernel
+    times per launch and picoseconds per key."""
+    import torch
+    import paper_2205_05982_gb300 as vq
+    vq.load()
+    lo, hi = (int(x) for x in args.leaf_sizes.split(","))
+    rng = np.random.default_rng(inputs.DEFAULT_SEED)
+    sizes = rng.integers(lo, hi + 1, size=args.n // ((lo + hi) // 2) + 1)
+    off = inputs.offsets_from_sizes(sizes)
+    n = int(off[-1])
+    a = inputs.make(args.dtype, n, "uniform", specials=args.dtype in ("f32", "f64"))
+    src = to_device_bits(a, args.dtype, torch)
+    offd = torch.from_numpy(off.astype(np.int64)).cuda()
+    ws = vq.alloc_workspace(args.dtype, n, sizes.size)
+    copies = [src.clone() for _ in range(args.steps + args.warmup)]
+    for i in range(args.warmup):
+        vq.sort_segmented_ws_(copies[i], offd, ws, args.dtype)
+    torch.cuda.synchronize()
+    vq.profile_reset()
+    vq.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for c in copies[args.warmup:]:
+        vq.sort_segmented_ws_(c, offd, ws, args.dtype)
+    e1.record()
+    torch.cuda.synchronize()
+    vq.profile_enable(False)
+    prof = vq.profile_read()
+    st = vq.stats(ws)
+    assert st["device_status"] == 0 and st["keys_partitioned"] == 0, st
+    ms = e0.elapsed_time(e1) / args.steps
+    keys = {"leaf_warp": st["leaf_keys_warp"], "leaf_mid": st["leaf_keys_mid"], "leaf_block": st["leaf_keys_block"]}
+    kern = {k: v["ms"] / max(1, v["launches"]) for k, v in prof.items()}
+    print(json.dumps({"workload": f"leaf microbenchmark: {n} {args.dtype} keys in {sizes.size} segments of "
+                                  f"{lo}..{hi} keys", "n_keys": n, "ms_per_step": ms,
+                      "gkeys_per_s": n / (ms * 1e-3) / 1e9, "kernels_ms": kern, "leaf_keys": keys,
+                      "ps_per_key": {k: kern[k] * 1e9 / keys[k] for k in keys if keys[k] and k in kern}}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.leaf_sizes:
+        run_leaf_sizes(args)
     else:
         run_gpu(args)
 
