@@ -1004,9 +1004,13 @@ __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *
   // the bucket's slots are reserved now; the atomic's result is first used
   // after the staging below, so its round trip overlaps the staging
   unsigned rel = 0;
+  unsigned long long lim = 0;
   if (tid < K) {
     s_tstart[tid] = (unsigned short)excl;
-    if (cnt) rel = atomicAdd(&kw.cnt[stripe][tid], cnt);
+    if (cnt) {
+      rel = atomicAdd(&kw.cnt[stripe][tid], cnt);
+      lim = __ldcg(&kw.start[tid + 1]);   // the bucket's end, for the guard below
+    }
     s_hist[tid] = 0;   // ready for the next tile
   }
   __syncthreads();
@@ -1032,7 +1036,7 @@ __device__ __forceinline__ void kw_scatter_tile(const SortArgs &a, const uint4 *
     // staged position p of this bucket goes to rbegin + off + p
     unsigned off = 0;
     if (cnt) {
-      if (rbegin + rel + cnt > __ldcg(&kw.start[tid + 1])) {   // guard: stay inside the bucket
+      if (rbegin + rel + cnt > lim) {   // guard: stay inside the bucket
         guard_failed(a, GUARD_BUCKET);
         off = ~0u;
       } else {
@@ -1241,21 +1245,35 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
   }
   __syncthreads();
   uint32_t phase = 0;
-  // Thread 0 state: the range whose descriptor is in s_seg, and the
-  // completion count of the previous tile, read one claim later so that the
-  // two round trips overlap.
-  unsigned seg_in_smem = ~0u, pend_sid = ~0u, pend_nt = 0, pend_phase = 0;
-  uint32_t pend_prev = 0;
-  // the next ticket, claimed while the current tile is processed
+  // Thread 0 state: the range whose descriptor is in s_seg, the next ticket
+  // (claimed while the current tile runs) and its queue word, read before the
+  // tile's last barrier so that the read overlaps the barrier.
+  unsigned seg_in_smem = ~0u;
   bool nclaimed = false;
-  unsigned long long nticket = 0;
+  unsigned long long nticket = 0, nword = 0;
+  // Thread FT state: the last tile's release add on its range's completion
+  // count, whose result FT reads at the next claim while thread 0 claims.
+  constexpr unsigned FT = NT - 32;
+  unsigned pend_sid = ~0u, pend_nt = 0, pend_phase = 0;
+  uint32_t pend_prev = 0;
 
   for (;;) {
     if (tid == 0) {
       const unsigned long long t = nclaimed ? nticket : atomicAdd(&a.hdr->head, 1ull);
-      nclaimed = false;
       unsigned long long item = 0;
-      const bool have = probe_ticket(a, t, item);
+      bool have;
+      if (nclaimed && (nword & ITEM_VALID)) {
+        item = nword;
+        have = true;
+      } else {
+        have = probe_ticket(a, t, item);
+      }
+      nclaimed = false;
+      if (have) prepare<KB, CPT>(a, item, s_item, s_seg, seg_in_smem, s_newtree, smem, &s_bar);
+      s_go = have;
+      s_ticket = t;
+    }
+    if (tid == FT) {
       int fin = 0;
       if (pend_sid != ~0u) {
         fin = pend_prev == pend_nt - 1;
@@ -1268,9 +1286,6 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
         pend_sid = ~0u;
       }
       s_fin = fin;
-      if (have) prepare<KB, CPT>(a, item, s_item, s_seg, seg_in_smem, s_newtree, smem, &s_bar);
-      s_go = have;
-      s_ticket = t;
     }
     __syncthreads();
     // the previous tile finished its range: the rest of Algorithm 1 for it
@@ -1379,15 +1394,17 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
           kw_scatter_tile<KB, KCPT, false>(a, sw, nwc, lo, hi, s_ids, K, kw, i % KW_STRIPES, b, dst, stage,
                                            s_sb, s_hist, s_tstart, s_off, s_w);
       }
+      const unsigned fnt = phase1 ? sg.ntiles : kw_count_items(sg.ntiles);   // s_seg changes after the barrier
+      if (tid == 0) nword = nticket < a.cap_q ? ld_acquire(&a.items[nticket]) : 0ull;
       fence_proxy_async_smem();   // the next TMA copy reuses the window
       __syncthreads();
       // a scatter tile leaves its bucket offsets in s_off: clear them for the
       // next counting tile (ordered before it by the barrier after the claim)
       if (phase1) s_off[tid] = 0;
-      if (tid == 0) {
+      if (tid == FT) {
         pend_prev = atom_add_release(&a.segs[sid].tiles_done, 1u);
         pend_sid = sid;
-        pend_nt = phase1 ? sg.ntiles : kw_count_items(sg.ntiles);
+        pend_nt = fnt;
         pend_phase = phase1;
       }
       continue;
@@ -1446,16 +1463,18 @@ __global__ void __launch_bounds__(NT, part_blocks_per_sm(CPT)) k_partition(SortA
       else if (raw) scatter_tile<KB, CPT, true, false>(a, sw, nwc, lo, hi, piv, outL, outR, runL, runR);
       else scatter_tile<KB, CPT, false, false>(a, sw, nwc, lo, hi, piv, outL, outR, runL, runR);
     }
+    const unsigned fnt = sg.ntiles;   // s_seg changes after the barrier
+    if (tid == 0) nword = nticket < a.cap_q ? ld_acquire(&a.items[nticket]) : 0ull;
     fence_proxy_async_smem();   // the next TMA copy reuses the window
     __syncthreads();
 
-    // ---- range completion: one release add by thread 0 covers the whole
+    // ---- range completion: one release add by thread FT covers the whole
     // block's stores (ordered before it by the barrier above); its result is
-    // read after the next claim
-    if (tid == 0) {
+    // read at the next claim
+    if (tid == FT) {
       pend_prev = atom_add_release(&a.segs[sid].tiles_done, 1u);
       pend_sid = sid;
-      pend_nt = sg.ntiles;
+      pend_nt = fnt;
       pend_phase = 0;
     }
   }
