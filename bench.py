@@ -138,8 +138,20 @@ def issue_peak():
 # Nominal HBM3e bandwidth of one GB300 (the measured copy bandwidth is the
 # main denominator; this one is reported beside it).
 NOMINAL_HBM_GBS = 8000.0
-# Leaf cutoff the library uses by key size when none is set.
+# Leaf cutoff the library uses by key size when none is set, for large
+# arrays and segmented batches.
 DEFAULT_LEAF_CUTOFF = {2: 4096, 4: 4096, 8: 4096, 16: 4096}
+# The library's size rule for one array of n keys (launch.h size_leaf_cutoff):
+# 16384 up to the small bound, 8192 below the mid bound.
+LEAF_N_SMALL = {"wide": 1 << 21, "narrow": 1 << 22}
+LEAF_N_MID = {"wide": 1 << 26, "narrow": 1 << 25}
+
+
+def default_leaf_cutoff(kb: int, n: int, segments: int = 1) -> int:
+    if segments != 1 or kb == 16:
+        return DEFAULT_LEAF_CUTOFF[kb]
+    w = "wide" if kb == 8 else "narrow"
+    return 16384 if n <= LEAF_N_SMALL[w] else 8192 if n < LEAF_N_MID[w] else DEFAULT_LEAF_CUTOFF[kb]
 
 
 def ideal_two_way(kb: int, n: int, cutoff: int) -> dict:
@@ -440,6 +452,7 @@ def extra_c1(vq, torch, reps=20):
            "gkeys_per_s": n / (med * 1e-3) / 1e9, "us_per_sort": med * 1e3,
            "us_p10": float(np.percentile(ms, 10)) * 1e3, "us_p90": float(np.percentile(ms, 90)) * 1e3,
            "sorts": reps, "l2": "256 MB written between timed sorts", "launches_per_sort": 7,
+           "leaf_cutoff": default_leaf_cutoff(8, n),
            "max_depth": st["max_depth"], "kway_ranges": st["kway_ranges"]}
     del t, src, ws, flush
     torch.cuda.empty_cache()
@@ -771,7 +784,7 @@ def run_gpu(args):
     achieved = part_bytes / (part_ms * 1e-3) / 1e9
     leaf_ms = sum(v["ms"] for k, v in prof.items() if k.startswith("leaf")) / args.steps
     sort_bytes = part_bytes + 2 * kb * args.n
-    ideal = ideal_two_way(kb, args.n, vq.get_option("leaf_cutoff") or DEFAULT_LEAF_CUTOFF[kb])
+    ideal = ideal_two_way(kb, args.n, vq.get_option("leaf_cutoff") or default_leaf_cutoff(kb, args.n))
     wl = f"{args.dtype}:{args.n}:{args.dist}"
     rooflines = {"partition": {
         "bound": "hbm", "kernel": "k_partition (persistent partition levels)", "achieved": achieved,

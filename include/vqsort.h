@@ -255,8 +255,11 @@ typedef enum vq_option {
   VQ_OPT_DEPTH_LIMIT = 0,   /* -1: 2*floor(log2 n)+4 per root range (default);
                                k >= 0: at most k partition levels (test hook for the
                                merge-sort fallback) */
-  VQ_OPT_LEAF_CUTOFF = 1,   /* 0: default per key size; else largest range (keys, a
-                               power of two in [1024, 16384] that fits 128 KiB of shared
+  VQ_OPT_LEAF_CUTOFF = 1,   /* 0 (default): by key size and array length: one array of
+                               at most 2^21 keys (keys of 4 bytes or fewer: 2^22) 16384,
+                               below 2^26 keys (2^25) 8192, else, and for segmented
+                               batches and 16-byte keys, 4096; else largest range (keys,
+                               a power of two in [1024, 16384] that fits 128 KiB of shared
                                memory) finished by the block network */
   VQ_OPT_SEED = 2,          /* seed of the per-range pivot sampling streams */
   VQ_OPT_SPIN_LIMIT = 3,    /* iterations of each bounded device wait (default 2^22,

@@ -387,7 +387,8 @@ __device__ __forceinline__ unsigned kway_bits(const SortArgs &a, uint64_t m) {
   return bits;
 }
 
-// Samples R*NT keys of [b, b+m) (64-byte chunks drawn as in sample_pivot),
+// Samples R*NT keys of [b, b+m) (whole 64-byte chunks at random positions,
+// as in sample_pivot, but drawn independently per chunk),
 // sorts them with the block network and takes splitter i = sample rank
 // i*S/K - 1 (i = 1..K-1). When those repeat a value (heavy duplicates) and
 // the distinct values d number at most 127, the range switches to equality
@@ -410,11 +411,11 @@ __device__ unsigned build_splitters(const void *buf, uint64_t b, uint64_t m, boo
   const uintptr_t addr = (uintptr_t)buf + b * kmem(KB);
   const uint64_t off = ((64 - (addr & 63)) & 63) / kmem(KB);
   const uint64_t nc = (m - off) / kc;
-  if (threadIdx.x == 0) {
-    Sfc64 r;
-    sfc_seed(r, seed);
-    for (unsigned j = 0; j < ns; ++j) s_chunk[j] = __umul64hi(sfc_next(r), nc);
-  }
+  // one draw per thread: the SplitMix64 finaliser of the range seed and the
+  // draw index (counter-based, so no thread waits on a sequential stream),
+  // bounded by multiply-high
+  for (unsigned j = threadIdx.x; j < ns; j += NT)
+    s_chunk[j] = __umul64hi(mix64(seed + 0x9E3779B97F4A7C15ull * (j + 1)), nc);
   __syncthreads();
   C k[R];
 #pragma unroll

@@ -67,11 +67,14 @@ int tile_cpt(int kb) {
   return g_tile_bytes == 16384 ? 4 : g_tile_bytes == 65536 ? 16 : 8;
 }
 
-unsigned leaf_cutoff_for(int kb) {
+// The leaf cutoff of a sort of n keys in `segments` arrays: the option if
+// set, else the size rule.
+unsigned leaf_cutoff_for(int kb, uint64_t n, uint64_t segments) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_leaf_cutoff > 0) return (unsigned)g_leaf_cutoff < max_leaf_cutoff(kb) ? (unsigned)g_leaf_cutoff
                                                                              : max_leaf_cutoff(kb);
-  return default_leaf_cutoff(kb);
+  const unsigned c = size_leaf_cutoff(kb, n, segments);
+  return c < max_leaf_cutoff(kb) ? c : max_leaf_cutoff(kb);
 }
 
 // ---------------------------------------------------------------------------
@@ -257,7 +260,7 @@ struct Job {
 
 vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   const int kb = key_bytes(j.dt);
-  const unsigned C = leaf_cutoff_for(kb);
+  const unsigned C = leaf_cutoff_for(kb, j.n, j.num_segments);
   int64_t depth_limit, seed, spin, stall, leaf_threads, kway;
   const int cpt = tile_cpt(kb);
   {
@@ -360,7 +363,8 @@ vq_status sort_common(vq_dtype dt, void *keys, uint64_t n, const uint64_t *offse
       std::lock_guard<std::mutex> lk(g_mu);
       dl = g_depth_limit;
     }
-    const Layout L = make_layout(kb, n, offsets ? S : 1, leaf_cutoff_for(kb), dl, true, tile_cpt(kb));
+    const uint64_t nseg = offsets ? S : 1;
+    const Layout L = make_layout(kb, n, nseg, leaf_cutoff_for(kb, n, nseg), dl, true, tile_cpt(kb));
     if ((st = owned_ws(s, L.total, &ws, &ws_bytes)) != VQ_OK) return st;
   }
   Job j{dt, keys, nullptr, n, offsets, offsets ? S : 1, asc, MODE_SORT, nullptr, nullptr};
@@ -435,7 +439,7 @@ vq_status host_enqueue(vq_dtype dt, void *h_keys, size_t n, int ascending, cudaS
     h_dev = attr.devicePointer;
   cudaGetLastError();
   if (cudaMemcpyAsync(dbuf, h_keys, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return VQ_ERR_CUDA;
-  const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb), dl, true, tile_cpt(kb));
+  const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb, n, 1), dl, true, tile_cpt(kb));
   void *ws;
   size_t wsb;
   vq_status st;
@@ -484,7 +488,8 @@ size_t vqsort_workspace_bytes(vq_dtype dt, size_t n_total, size_t num_segments) 
     std::lock_guard<std::mutex> lk(g_mu);
     dl = g_depth_limit;
   }
-  return make_layout(kb, n_total, num_segments ? num_segments : 1, leaf_cutoff_for(kb), dl, true, 4).total;
+  const uint64_t S = num_segments ? num_segments : 1;
+  return make_layout(kb, n_total, S, leaf_cutoff_for(kb, n_total, S), dl, true, 4).total;
 }
 
 vq_status vqsort_sort_ws(vq_dtype dt, void *d_keys, size_t n, int ascending, void *d_ws, size_t ws_bytes,
@@ -536,7 +541,7 @@ vq_status vqsort_partition(vq_dtype dt, const void *d_in, void *d_out, size_t n,
   if ((st = check_device()) != VQ_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const int kb = key_bytes(dt);
-  const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb), -1, false, tile_cpt(kb));
+  const Layout L = make_layout(kb, n, 1, leaf_cutoff_for(kb, n, 1), -1, false, tile_cpt(kb));
   void *ws;
   size_t wsb;
   if ((st = owned_ws(s, L.total, &ws, &wsb)) != VQ_OK) return st;
@@ -562,7 +567,7 @@ vq_status vqsort_sort_stable(vq_dtype dt, void *d_keys, size_t n, int ascending,
     std::lock_guard<std::mutex> lk(g_mu);
     dl = g_depth_limit;
   }
-  const Layout L = make_layout(pkb, n, 1, leaf_cutoff_for(pkb), dl, true, tile_cpt(pkb));
+  const Layout L = make_layout(pkb, n, 1, leaf_cutoff_for(pkb, n, 1), dl, true, tile_cpt(pkb));
   const size_t packed_off = align256(L.total);
   void *ws;
   size_t wsb;

@@ -307,14 +307,30 @@ def test_kway_mid_sizes_with_workspace(vq, oracle_mod, n):
     ("u128", 16_384), ("u128", 700_001), ("kv64", 400_009), ("f64", 20_000_003)])
 def test_kway_bucket_counts(vq, oracle_mod, dtype, n):
     """Range sizes that give 16, 32, ..., 256 buckets (about a quarter of the
-    leaf cutoff per bucket), and sizes whose buckets are split again, K ways
-    or in two."""
-    a = make(dtype, n, "uniform", seed=n % 1009)
-    check_sort(vq, oracle_mod, dtype, a, True)
-    st = vq.stats()
+    4096-key leaf cutoff per bucket), and sizes whose buckets are split again,
+    K ways or in two."""
+    vq.set_option("leaf_cutoff", 4096)
+    try:
+        a = make(dtype, n, "uniform", seed=n % 1009)
+        check_sort(vq, oracle_mod, dtype, a, True)
+        st = vq.stats()
+    finally:
+        vq.set_option("leaf_cutoff", 0)
     assert st["kway_ranges"] >= 1
     assert st["keys_counted"] >= n            # the root range was counted
     assert st["leaf_keys"] + st["equal_keys"] + st["fallback_keys"] == n
+
+
+@pytest.mark.parametrize("dtype,n,depth", [("u64", 1_000_000, 1), ("u32", 1_000_000, 1), ("f64", 500_000, 1)])
+def test_short_arrays_default_cutoff(vq, oracle_mod, dtype, n, depth):
+    """With no cutoff set, a short array takes the 16384-key cutoff: one
+    K-way level of 256 buckets leaves only leaves (a 4096-key cutoff would
+    split most buckets again)."""
+    a = make(dtype, n, "uniform", seed=5)
+    check_sort(vq, oracle_mod, dtype, a, True)
+    st = vq.stats()
+    assert st["kway_ranges"] == 1
+    assert st["max_depth"] == depth
 
 
 @pytest.mark.parametrize("tile", (16384, 65536))

@@ -122,6 +122,21 @@ def test_bench_default_cutoffs_match_library():
     for kb in (2, 4, 8, 16):
         assert bench.DEFAULT_LEAF_CUTOFF[kb] == lib(kb)
 
+    # the size rule's bounds
+    def const(name):
+        return int(re.search(name + r" = 1ull << (\d+)", src).group(1))
+    assert bench.LEAF_N_SMALL == {"wide": 1 << const("LEAF_N_SMALL_WIDE"), "narrow": 1 << const("LEAF_N_SMALL_NARROW")}
+    assert bench.LEAF_N_MID == {"wide": 1 << const("LEAF_N_MID_WIDE"), "narrow": 1 << const("LEAF_N_MID_NARROW")}
+    # 16384 for short arrays, 8192 for mid-size ones, the default for large
+    # ones, segmented batches and 16-byte keys
+    assert bench.default_leaf_cutoff(8, 10**6) == 16384
+    assert bench.default_leaf_cutoff(8, 3 * 10**7) == 8192
+    assert bench.default_leaf_cutoff(8, 10**8) == 4096
+    assert bench.default_leaf_cutoff(4, 4 * 10**6) == 16384
+    assert bench.default_leaf_cutoff(4, 6 * 10**7) == 4096
+    assert bench.default_leaf_cutoff(8, 10**6, segments=16) == 4096
+    assert bench.default_leaf_cutoff(16, 10**6) == 4096
+
 
 def test_reference_sample_is_bounded():
     import bench
