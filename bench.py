@@ -82,6 +82,9 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the per-dtype, batched and served measurements")
     p.add_argument("--served-requests", type=int, default=10_000)
+    p.add_argument("--leaf-cutoff", type=int, default=0,
+                   help="leaf cutoff option (0: the library's rule for the array length); lets a profiling "
+                        "run of a smaller array keep the partition levels of a larger one")
     p.add_argument("--leaf-sizes", default=None,
                    help="LO,HI: leaf microbenchmark instead: --n keys in segments of LO..HI keys (each at most "
                         "the leaf cutoff, so every segment goes straight to a leaf kernel)")
@@ -179,6 +182,7 @@ def workload(args):
         "n_keys": args.n, "key_type": args.dtype, "distribution": args.dist,
         "seed": inputs.DEFAULT_SEED,
         "l2": "inputs larger than L2 (one fresh array per timed step)",
+        "leaf_cutoff": getattr(args, "leaf_cutoff", 0) or default_leaf_cutoff(inputs.KEY_BYTES[args.dtype], args.n),
     }
 
 
@@ -723,6 +727,8 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     vq.load()
+    if args.leaf_cutoff:
+        vq.set_option("leaf_cutoff", args.leaf_cutoff)
     kb = inputs.KEY_BYTES[args.dtype]
 
     a = make_input(args)
@@ -983,6 +989,7 @@ def run_gpu(args):
     }
     if rank == 0:
         if not args.no_extras:
+            vq.set_option("leaf_cutoff", 0)   # the extra workloads take the library's rule
             del src
             torch.cuda.empty_cache()
             line["c1"] = extra_c1(vq, torch)
