@@ -521,7 +521,7 @@ def extra_wide(vq, torch, peak, n=25_000_000):
         part_ms = part["ms"] / max(1, part["launches"])
         out[dt] = {"gkeys_per_s": n / (ms * 1e-3) / 1e9, "ms": ms,
                    "partition_frac": partition_bytes(16, st) / (part_ms * 1e-3) / 1e9 / peak,
-                   "leaf_ms": sum(v["ms"] for k, v in prof.items() if k.startswith("leaf")) / max(1, part["launches"])}
+                   "leaf_ms": prof.get("leaves", {"ms": float("nan")})["ms"] / max(1, part["launches"])}
         del copies, src, ws
         torch.cuda.empty_cache()
     return out
@@ -788,7 +788,7 @@ def run_gpu(args):
     part_ms = per_launch_ms("partition")
     part_bytes = partition_bytes(kb, st)
     achieved = part_bytes / (part_ms * 1e-3) / 1e9
-    leaf_ms = sum(v["ms"] for k, v in prof.items() if k.startswith("leaf")) / args.steps
+    leaf_ms = per_launch_ms("leaves")   # the leaf phase, fork to join (its kernels overlap)
     sort_bytes = part_bytes + 2 * kb * args.n
     ideal = ideal_two_way(kb, args.n, vq.get_option("leaf_cutoff") or default_leaf_cutoff(kb, args.n))
     wl = f"{args.dtype}:{args.n}:{args.dist}"
@@ -797,6 +797,11 @@ def run_gpu(args):
         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
         "traffic": recorded_traffic(wl, KERNEL_SOURCES), "algorithmic_bytes_per_launch": part_bytes,
         "overhead_bytes_per_launch": partition_overhead_bytes(kb, st), "ms_per_launch": part_ms}}
+    # The three leaf kernels run at once (block and warp leaves on side
+    # streams forked from the sort's stream, mid leaves on it), so a leaf
+    # kernel's time per launch includes time it shares the GPU with the
+    # others; the leaf phase is read as a whole ("leaves", fork to join) as
+    # well, and that is the figure compared with the partition.
     for name in ("leaf_block", "leaf_mid", "leaf_warp"):
         ms_l = per_launch_ms(name)
         byts = leaf_bytes(kb, st, name)
@@ -804,27 +809,39 @@ def run_gpu(args):
         rooflines[name] = {"bound": "hbm", "kernel": f"k_{name}", "achieved": got, "peak": peak, "unit": "GB/s",
                            "frac": got / peak, "peak_source": peak_kind,
                            "traffic": recorded_traffic(f"{name}:{wl}", LEAF_SOURCES),
-                           "algorithmic_bytes_per_launch": byts, "ms_per_launch": ms_l}
-    # the leaf sorts are bound by the integer ALU pipe: their ALU-pipe warp
-    # instructions per launch (ncu, recorded) over the measured ALU-pipe
-    # rate of the throughput probe explain the low HBM fraction
+                           "algorithmic_bytes_per_launch": byts, "ms_per_launch": ms_l,
+                           "concurrent_with": [k for k in ("leaf_block", "leaf_mid", "leaf_warp") if k != name]}
+    # The leaf sorts are bound by the integer ALU pipe: the phase's ALU-pipe
+    # warp instructions (ncu, recorded for the mid and block kernels; the
+    # warp leaves, under 1 % of the keys, are not recorded) over the measured
+    # ALU-pipe rate of the throughput probe; the HBM reading is beside it.
+    leaf_total = sum(rooflines[k]["algorithmic_bytes_per_launch"] for k in ("leaf_block", "leaf_mid", "leaf_warp"))
+    got = leaf_total / (leaf_ms * 1e-3) / 1e9 if leaf_ms > 0 else 0.0
+    traffic = [rooflines[k]["traffic"] for k in ("leaf_block", "leaf_mid")]
     ipk = issue_peak()
-    for name in ("leaf_block", "leaf_mid"):
-        alu = recorded_traffic(f"{name}:{wl}", LEAF_SOURCES, "alu_inst_per_launch")
-        inst = recorded_traffic(f"{name}:{wl}", LEAF_SOURCES, "inst_per_launch")
-        r = rooflines[name]
-        keys = r["algorithmic_bytes_per_launch"] / (2 * kb)
-        r["alu"] = {"alu_inst_per_launch": alu, "inst_per_launch": inst,
-                    "thread_inst_per_key": inst * 32 / keys if inst and keys else None,
-                    "achieved_alu_inst_per_s": alu / (r["ms_per_launch"] * 1e-3) if alu else None,
-                    "peak_alu_inst_per_s": ipk["warp_inst_per_s"],
-                    "frac": alu / (r["ms_per_launch"] * 1e-3) / ipk["warp_inst_per_s"] if alu else None,
-                    "comparisons_per_key": st["leaf_ce"] / max(1, st["leaf_keys"])}
-    dominant = max(rooflines, key=lambda k: rooflines[k]["ms_per_launch"]
+    alus = [recorded_traffic(f"{k}:{wl}", LEAF_SOURCES, "alu_inst_per_launch") for k in ("leaf_block", "leaf_mid")]
+    insts = [recorded_traffic(f"{k}:{wl}", LEAF_SOURCES, "inst_per_launch") for k in ("leaf_block", "leaf_mid")]
+    alu = sum(alus) if all(alus) else None
+    inst = sum(insts) if all(insts) else None
+    keys = (st["leaf_keys_block"] + st["leaf_keys_mid"]) or 1
+    alu_rate = alu / (leaf_ms * 1e-3) if alu and leaf_ms > 0 else None
+    rooflines["leaves"] = {
+        "bound": "alu", "kernel": "k_leaf_block + k_leaf_mid + k_leaf_warp (one phase, fork to join)",
+        "achieved": alu_rate, "peak": ipk["warp_inst_per_s"], "unit": "ALU-pipe warp instructions/s",
+        "frac": alu_rate / ipk["warp_inst_per_s"] if alu_rate else None,
+        "peak_source": "measured (vqsort_probe_int_throughput)",
+        "traffic": sum(traffic) if all(traffic) else None, "ms_per_launch": leaf_ms,
+        "alu_inst_per_launch": alu, "inst_per_launch": inst,
+        "thread_inst_per_key": inst * 32 / keys if inst else None,
+        "comparisons_per_key": st["leaf_ce"] / max(1, st["leaf_keys"]),
+        "hbm": {"achieved": got, "peak": peak, "unit": "GB/s", "frac": got / peak, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": leaf_total}}
+    # the dominant step: the partition or the leaf phase, whichever is longer
+    dominant = max(("partition", "leaves"), key=lambda k: rooflines[k]["ms_per_launch"]
                    if rooflines[k]["ms_per_launch"] == rooflines[k]["ms_per_launch"] else -1)
     kernels = {k: {"ms_per_launch": v["ms"] / max(1, v["launches"]), "launches": v["launches"]}
-               for k, v in prof.items()}
-    gpu_launches = sum(v["launches"] for v in prof.values())
+               for k, v in prof.items() if k != "leaves"}
+    gpu_launches = sum(v["launches"] for k, v in prof.items() if k != "leaves")
 
     # end to end through the public host-buffer API: every step uploads its
     # own pinned array, sorts it and brings the keys back into it; steps
@@ -955,7 +972,7 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.dtype, "data": "synthetic",
         "config": workload(args),
-        "roofline": dict(rooflines[dominant], dominant_of=sorted(rooflines)),
+        "roofline": dict(rooflines[dominant], dominant_of=["leaves", "partition"]),
         "rooflines": rooflines,
         "issue_peak": ipk,
         "sort_roofline": {"how": "2 x key bytes x (keys of every partition level actually run + the leaf "

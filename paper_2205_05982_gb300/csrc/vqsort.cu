@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -174,6 +175,53 @@ const void *lookup_ws(cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// Side streams of the leaf kernels, one pair per (device, stream). After the
+// partition the leaf kernels write disjoint ranges and never wait on one
+// another, so two of them run on side streams that fork from the caller's
+// stream and join it again through events (a CUDA-graph capture of the
+// caller's stream takes the fork and the join in as well). Created on the
+// first sort on a stream that is not being captured; until then, and if
+// creation fails, the leaf kernels run one after another on the caller's
+// stream.
+// ---------------------------------------------------------------------------
+struct Fork {
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+  std::mutex mu;   // one fork/join sequence at a time per caller stream
+};
+std::map<std::pair<int, cudaStream_t>, std::unique_ptr<Fork>> g_fork;
+
+Fork *fork_for(cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  std::unique_ptr<Fork> &f = g_fork[{dev, s}];
+  if (f) return f.get();
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  auto nf = std::make_unique<Fork>();
+  bool ok = cudaEventCreateWithFlags(&nf->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < 2 && ok; ++i) {
+    ok = cudaStreamCreateWithFlags(&nf->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&nf->join[i], cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    for (int i = 0; i < 2; ++i) {
+      if (nf->side[i]) cudaStreamDestroy(nf->side[i]);
+      if (nf->join[i]) cudaEventDestroy(nf->join[i]);
+    }
+    if (nf->fork) cudaEventDestroy(nf->fork);
+    return nullptr;
+  }
+  f = std::move(nf);
+  return f.get();
+}
+
+// ---------------------------------------------------------------------------
 // Per-kernel timing.
 // ---------------------------------------------------------------------------
 struct ProfEntry {
@@ -331,9 +379,37 @@ vq_status run(const Job &j, void *ws, size_t ws_bytes, cudaStream_t s) {
   if ((e = timed("seed", s, [&] { return launch_seed(kc, a, s); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed("partition", s, [&] { return launch_partition(kc, a, s); })) != cudaSuccess) return cuda_status(e);
   if (j.mode == MODE_SORT) {
-    if ((e = timed("leaf_warp", s, [&] { return launch_leaf_warp(kc, a, s); })) != cudaSuccess) return cuda_status(e);
-    if ((e = timed("leaf_mid", s, [&] { return launch_leaf_mid(kc, a, s); })) != cudaSuccess) return cuda_status(e);
-    if ((e = timed("leaf_block", s, [&] { return launch_leaf_block(kc, a, s); })) != cudaSuccess) return cuda_status(e);
+    // the leaf phase, timed as a whole ("leaves") as well as per kernel:
+    // with the fork its kernels overlap
+    Fork *fk = fork_for(s);
+    e = timed("leaves", s, [&]() -> cudaError_t {
+      cudaError_t x;
+      if (!fk) {
+        if ((x = timed("leaf_warp", s, [&] { return launch_leaf_warp(kc, a, s); })) != cudaSuccess) return x;
+        if ((x = timed("leaf_mid", s, [&] { return launch_leaf_mid(kc, a, s); })) != cudaSuccess) return x;
+        return timed("leaf_block", s, [&] { return launch_leaf_block(kc, a, s); });
+      }
+      // block leaves and warp leaves on the side streams, mid leaves here;
+      // the join is enqueued even when a launch failed
+      std::lock_guard<std::mutex> flk(fk->mu);
+      cudaStream_t b = fk->side[0], w = fk->side[1];
+      x = cudaEventRecord(fk->fork, s);
+      if (x == cudaSuccess) x = cudaStreamWaitEvent(b, fk->fork, 0);
+      if (x == cudaSuccess) x = cudaStreamWaitEvent(w, fk->fork, 0);
+      if (x != cudaSuccess) return x;
+      const cudaError_t eb = timed("leaf_block", b, [&] { return launch_leaf_block(kc, a, b); });
+      const cudaError_t ew = timed("leaf_warp", w, [&] { return launch_leaf_warp(kc, a, w); });
+      const cudaError_t em = timed("leaf_mid", s, [&] { return launch_leaf_mid(kc, a, s); });
+      x = cudaEventRecord(fk->join[0], b);
+      if (x == cudaSuccess) x = cudaEventRecord(fk->join[1], w);
+      if (x == cudaSuccess) x = cudaStreamWaitEvent(s, fk->join[0], 0);
+      if (x == cudaSuccess) x = cudaStreamWaitEvent(s, fk->join[1], 0);
+      for (cudaError_t y : {eb, ew, em})
+        if (y != cudaSuccess) return y;
+      return x;
+    });
+    if (e != cudaSuccess) return cuda_status(e);
+    // cooperative (its blocks must be resident together): after the join
     if ((e = timed("fallback", s, [&] { return launch_fallback(kc, a, s); })) != cudaSuccess) return cuda_status(e);
   }
   return VQ_OK;
