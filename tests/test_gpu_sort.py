@@ -147,6 +147,48 @@ def test_explicit_workspace_and_graph_capture(vq, oracle_mod):
         assert same_bits(to_host(t, "u64", src), oracle_mod.sort(src, "u64"))
 
 
+def test_graph_capture_on_a_fresh_stream(vq, oracle_mod):
+    """A stream whose first sort is captured has no side streams yet: its leaf
+    kernels are captured one after another on it, and the replay is exact."""
+    import torch
+    n = 700_001
+    a = inputs.make("i64", n, "uniform", seed=31)
+    t = to_dev(a, "i64")
+    ws = vq.alloc_workspace("i64", n)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        vq.sort_ws_(t, ws, "i64")
+    for seed in (32, 33):
+        b = inputs.make("i64", n, "uniform", seed=seed)
+        t.copy_(to_dev(b, "i64"))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert same_bits(to_host(t, "i64", b), oracle_mod.sort(b, "i64"))
+
+
+def test_sorts_interleaved_on_two_streams(vq, oracle_mod):
+    """Sorts enqueued alternately on two streams, each with its own workspace
+    and its own side streams for the leaf kernels, with no synchronisation
+    between them, are each exact."""
+    import torch
+    n = 2_000_003
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    wss = [vq.alloc_workspace("u64", n) for _ in streams]
+    arrays = [inputs.make("u64", n, "uniform", seed=40 + i) for i in range(6)]
+    devs = [to_dev(x, "u64") for x in arrays]
+    torch.cuda.synchronize()
+    for i, t in enumerate(devs):
+        with torch.cuda.stream(streams[i % 2]):
+            vq.sort_ws_(t, wss[i % 2], "u64")
+    torch.cuda.synchronize()
+    for s, w in zip(streams, wss):
+        assert vq.last_device_status(w, s) == 0
+    for x, t in zip(arrays, devs):
+        assert same_bits(to_host(t, "u64", x), oracle_mod.sort(x, "u64"))
+
+
 @pytest.mark.parametrize("kway", (0, 1))
 @pytest.mark.parametrize("dtype", ("u32", "i64", "f64", "u128"))
 @pytest.mark.parametrize("limit", (0, 1, 3))
