@@ -215,6 +215,17 @@ vq_status vqsort_last_device_status(const void *d_ws, void *stream);
    null pointers. */
 vq_status vqsort_device_status_async(const void *d_ws, uint64_t *h_status, void *stream);
 
+/* Library resource management (the paper has no counterpart). Waits for
+   `stream`, then frees what the library holds for it on the current device:
+   the workspace it allocated for sorts given none (vqsort_sort and the
+   other forms without a workspace argument), and the two side streams and
+   three events on which a sort runs its leaf kernels concurrently. The next
+   sort on the stream creates them again. For callers that create and
+   destroy streams, e.g. one per request. No sort may be enqueued on the
+   stream while this runs. VQ_ERR_CUDA if the wait fails (nothing is freed
+   then); VQ_OK when nothing was held. */
+vq_status vqsort_release_stream(void *stream);
+
 /* Counters of the last sort on a workspace (waits for `stream`). */
 typedef struct vq_stats {
   uint64_t keys_partitioned;     /* sum over partition levels (two-way and K-way) of keys

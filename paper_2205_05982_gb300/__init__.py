@@ -81,6 +81,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "vqsort_sort_host_async": ([i32, vp, sz, i32, vp], i32),
         "vqsort_sort_segmented": ([i32, vp, sz, vp, sz, i32, vp], i32),
         "vqsort_workspace_bytes": ([i32, sz, sz], sz),
+        "vqsort_release_stream": ([vp], i32),
         "vqsort_sort_ws": ([i32, vp, sz, i32, vp, sz, vp], i32),
         "vqsort_sort_segmented_ws": ([i32, vp, sz, vp, sz, i32, vp, sz, vp], i32),
         "vqsort_sort_host": ([i32, vp, sz, i32], i32),
@@ -338,6 +339,12 @@ def stats(ws=None, stream=None) -> dict:
     st = Stats()
     _check(load().vqsort_get_stats(_ws_arg(ws), _stream(stream), ctypes.byref(st)), "vqsort_get_stats")
     return {f: int(getattr(st, f)) for f, _ in Stats._fields_}
+
+
+def release_stream(stream=None):
+    """Frees the library's workspace and side streams for `stream` (default:
+    the current stream) after waiting for it."""
+    _check(load().vqsort_release_stream(_stream(stream)), "vqsort_release_stream")
 
 
 def status_string(status: int) -> str:

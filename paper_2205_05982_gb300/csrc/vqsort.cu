@@ -692,6 +692,39 @@ vq_status vqsort_device_status_async(const void *d_ws, uint64_t *h_status, void 
                                      (cudaStream_t)stream));
 }
 
+vq_status vqsort_release_stream(void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VQ_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return VQ_ERR_CUDA;
+  std::unique_ptr<Fork> f;
+  OwnedWs w;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_fork.find({dev, s});
+    if (it != g_fork.end()) {
+      f = std::move(it->second);
+      g_fork.erase(it);
+    }
+    auto jt = g_ws.find({dev, s});
+    if (jt != g_ws.end()) {
+      w = jt->second;
+      g_ws.erase(jt);
+    }
+  }
+  bool ok = true;
+  if (f) {
+    // the joins the stream waited for mean the side streams are idle too
+    for (int i = 0; i < 2; ++i) {
+      ok = cudaStreamDestroy(f->side[i]) == cudaSuccess && ok;
+      ok = cudaEventDestroy(f->join[i]) == cudaSuccess && ok;
+    }
+    ok = cudaEventDestroy(f->fork) == cudaSuccess && ok;
+  }
+  if (w.ptr) ok = cudaFree(w.ptr) == cudaSuccess && ok;
+  return ok ? VQ_OK : VQ_ERR_CUDA;
+}
+
 vq_status vqsort_get_stats(const void *d_ws, void *stream, vq_stats *out) {
   if (!out) return VQ_ERR_INVALID;
   Header h;

@@ -189,6 +189,24 @@ def test_sorts_interleaved_on_two_streams(vq, oracle_mod):
         assert same_bits(to_host(t, "u64", x), oracle_mod.sort(x, "u64"))
 
 
+def test_release_stream(vq, oracle_mod):
+    """Releasing a stream frees the library's workspace and side streams for
+    it; the next sort on the stream creates them again and is exact."""
+    import torch
+    s = torch.cuda.Stream()
+    for seed in (51, 52):
+        a = inputs.make("u64", 1_000_003, "uniform", seed=seed)
+        t = to_dev(a, "u64")
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            vq.sort_(t, "u64")
+        s.synchronize()
+        assert vq.last_device_status(None, s) == 0
+        assert same_bits(to_host(t, "u64", a), oracle_mod.sort(a, "u64"))
+        vq.release_stream(s)
+    vq.release_stream(s)   # nothing held: a no-op
+
+
 @pytest.mark.parametrize("kway", (0, 1))
 @pytest.mark.parametrize("dtype", ("u32", "i64", "f64", "u128"))
 @pytest.mark.parametrize("limit", (0, 1, 3))
