@@ -202,10 +202,17 @@ Fork *fork_for(cudaStream_t s) {
     cudaGetLastError();
     return nullptr;
   }
+  // the side streams take the caller's stream priority, so that a
+  // high-priority sort stays high-priority through its leaf phase
+  int prio = 0;
+  if (cudaStreamGetPriority(s, &prio) != cudaSuccess) {
+    cudaGetLastError();
+    prio = 0;
+  }
   auto nf = std::make_unique<Fork>();
   bool ok = cudaEventCreateWithFlags(&nf->fork, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; i < 2 && ok; ++i) {
-    ok = cudaStreamCreateWithFlags(&nf->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+    ok = cudaStreamCreateWithPriority(&nf->side[i], cudaStreamNonBlocking, prio) == cudaSuccess &&
          cudaEventCreateWithFlags(&nf->join[i], cudaEventDisableTiming) == cudaSuccess;
   }
   if (!ok) {

@@ -189,6 +189,22 @@ def test_sorts_interleaved_on_two_streams(vq, oracle_mod):
         assert same_bits(to_host(t, "u64", x), oracle_mod.sort(x, "u64"))
 
 
+def test_high_priority_stream(vq, oracle_mod):
+    """A sort on a high-priority stream (its leaf kernels' side streams take
+    that priority) is exact."""
+    import torch
+    s = torch.cuda.Stream(priority=-1)
+    a = inputs.make("f32", 3_000_017, "uniform", seed=61)
+    t = to_dev(a, "f32")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        vq.sort_(t, "f32", descending=True)
+    s.synchronize()
+    assert vq.last_device_status(None, s) == 0
+    assert same_bits(to_host(t, "f32", a), oracle_mod.sort(a, "f32", False))
+    vq.release_stream(s)
+
+
 def test_release_stream(vq, oracle_mod):
     """Releasing a stream frees the library's workspace and side streams for
     it; the next sort on the stream creates them again and is exact."""
