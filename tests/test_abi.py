@@ -74,6 +74,23 @@ def test_workspace_bytes_grows_with_n(lib):
     assert vq.workspace_bytes("u64", 10**6, 1000) > a
 
 
+def test_workspace_bytes_monotone_across_the_size_rules(lib):
+    """A workspace sized for N keys covers every sort of n <= N keys: the
+    default leaf cutoff and tile window change with n (16384 / 8192 / 4096
+    keys; 16 KiB windows for short arrays), so the size must still grow with
+    n across their bounds, for one array and for segmented batches."""
+    import paper_2205_05982_gb300 as vq
+    points = set()
+    for b in (1 << 21, 1 << 22, 1 << 25, 1 << 26):
+        points.update((b - 1, b, b + 1))
+    points.update((2, 1000, 4096, 16384, 65536, 10**6, 10**7, 10**8, 3 * 10**8))
+    points = sorted(points)
+    for dt in ("i16", "u32", "f32", "u64", "f64", "u128", "kv64"):
+        for segs in (1, 64):
+            sizes = [vq.workspace_bytes(dt, n, segs) for n in points]
+            assert all(x <= y for x, y in zip(sizes, sizes[1:])), (dt, segs, list(zip(points, sizes)))
+
+
 def _golden_pairs(name):
     rows = []
     for line in open(os.path.join(ROOT, "tests", "golden", name)):
