@@ -279,8 +279,8 @@ typedef enum vq_option {
                                block's bounded wait for work runs out and the sort reports
                                VQ_ERR_TIMEOUT (test of the bounded-wait path; never hangs) */
   VQ_OPT_TILE_BYTES = 5,    /* partition tile window: 16384, 32768 or 65536 bytes; 0 (default):
-                               16 KiB for a sort of one array short enough for the 16384-key
-                               leaf cutoff (keys of up to 8 bytes), else 64 KiB for 8- and
+                               16 KiB for a sort of one array of 4- or 8-byte keys short
+                               enough for the 16384-key leaf cutoff, else 64 KiB for 8- and
                                16-byte keys and 32 KiB for narrower keys */
   VQ_OPT_LEAF_THREADS = 6,  /* 0: block leaves use cutoff/16 threads (16 keys per thread);
                                256, 512 or 1024: that many threads when they hold a

@@ -69,18 +69,19 @@ int tile_cpt(int kb) {
 }
 
 // Tile windows of a sort of n keys in `segments` arrays: the option if set;
-// else 16 KiB windows for one array short enough for the 16384-key leaf
-// cutoff (keys of up to 8 bytes): its one K-way level has few tiles, and
-// more, smaller tiles keep more of the grid busy (L2 flushed: 1e6 u64 keys
-// 151 -> 131 us, 2.5e5 127 -> 106 us, 1e6 u32 118 -> 102 us); else the
-// per-key-size default.
+// else 16 KiB windows for one array of 4- or 8-byte keys short enough for
+// the 16384-key leaf cutoff: its one K-way level has few tiles, and more,
+// smaller tiles keep more of the grid busy (L2 flushed: 1e6 u64 keys
+// 151 -> 131 us, 2.5e5 127 -> 106 us, 1e6 u32 118 -> 102 us). 2-byte keys'
+// K-way tiles are the same size in 16 and 32 KiB windows, so they keep the
+// per-key-size default, as do 16-byte keys.
 int sort_tile_cpt(int kb, uint64_t n, uint64_t segments) {
   bool opt;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     opt = g_tile_bytes != 0;
   }
-  if (!opt && kmem(kb) <= 8 && size_leaf_cutoff(kb, n, segments) == 16384u) return 4;
+  if (!opt && (kmem(kb) == 4 || kmem(kb) == 8) && size_leaf_cutoff(kb, n, segments) == 16384u) return 4;
   return tile_cpt(kb);
 }
 
